@@ -1,0 +1,201 @@
+/*
+ * btree.h -- C ABI of the GB300 b-tree neighbour search.
+ *
+ * The method is the b-tree of "Finding Neighbors in a Forest: A b-tree for
+ * Smoothed Particle Hydrodynamics Simulations" (arXiv:1910.02639):
+ *   BuildTree     (Algorithm 1; Eq. 1 branching factor, Eq. 2 sub-cell
+ *                  coordinates, Eq. 3 sub-cell id, Eq. 4 distribution ratio)
+ *   FindNeighbors (Algorithm 2; Eqs. 5-6 range of sub-cells to visit)
+ * plus the SPH density sum with the M4 cubic spline as a consumer of the
+ * neighbour lists (the SPH interpolation of Sec. 1).
+ *
+ * Conventions shared by every call:
+ *  - Pointers marked "device" are CUDA device pointers (cudaMalloc, a
+ *    PyTorch CUDA tensor's data_ptr, ...) owned by the caller; the library
+ *    never frees them.  Pointers marked "host" are ordinary host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it.
+ *  - Particle indices are int32: n must be < 2^31 and n * ngmax < 2^62.
+ *  - k = 3 spatial dimensions (Table 1).
+ *  - Every call returns a status (bt_status).  Negative values are errors and
+ *    leave the outputs unspecified; positive values are warnings.
+ *  - Arithmetic contract: the tree (branching factors, cell membership) is the
+ *    one an IEEE binary64 evaluation of Eqs. 1-4 gives, with the readings
+ *    listed beside btree_build; the neighbour predicate is the binary64
+ *    D = ((dx*dx + dy*dy) + dz*dz) < (2 h_i)^2, no FMA contraction, with
+ *    dx = x_j - x_i from the float inputs.  Results are therefore identical
+ *    to a plain CPU evaluation of the same definitions.
+ */
+#ifndef BTREE_GB300_H
+#define BTREE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct btree btree_t; /* opaque; owns its device buffers */
+
+typedef enum {
+    BT_OK = 0,
+    BT_ERR_ARG = -1,        /* an argument is out of range or NULL          */
+    BT_ERR_OOM = -2,        /* a device allocation failed                   */
+    BT_ERR_CUDA = -3,       /* a CUDA call or kernel launch failed          */
+    BT_ERR_TIMEOUT = -4,    /* a bounded device-side wait gave up           */
+    BT_ERR_NONFINITE = -5,  /* a position or h is NaN/Inf, or h < 0         */
+    BT_ERR_CAPACITY = -6,   /* a fixed-size buffer was too small            */
+    BT_WARN_NGMAX = 1,      /* some particle has more than ngmax neighbours;
+                               its row holds the ngmax smallest indices and
+                               counts[i] holds the full count               */
+    BT_WARN_OVERSIZED_LEAF = 2 /* some leaf holds more than s particles
+                               (coincident particles or depth limit 32)     */
+} bt_status;
+
+/* Stream-ordered device allocator used for the tree's internal buffers.
+ * alloc(ctx, bytes, stream) returns a device pointer or NULL;
+ * free(ctx, ptr, stream) releases it.  Pass NULL to use cudaMallocAsync /
+ * cudaFreeAsync on the call's stream. */
+typedef struct {
+    void *ctx;
+    void *(*alloc)(void *ctx, size_t bytes, void *stream);
+    void (*free)(void *ctx, void *ptr, void *stream);
+} bt_allocator;
+
+/* Summary of a built tree (host struct filled by btree_get_info). */
+typedef struct {
+    int64_t n;               /* particles                                      */
+    int32_t bucket_size;     /* s                                              */
+    int32_t max_depth;       /* deepest node (root = 0)                        */
+    int64_t num_nodes;       /* internal nodes (the root counts if split)      */
+    int64_t num_slots;       /* sub-cells of all internal nodes (sum of b^3)   */
+    int64_t num_groups;      /* query groups of <= 32 particles used by find   */
+    int32_t root_b;          /* branching factor chosen at the root (0: leaf)  */
+    int32_t num_oversized;   /* leaves holding more than s particles           */
+    double build_ms;         /* device time of the last build (0 if unknown)   */
+} bt_info;
+
+/*
+ * btree_build -- BuildTree (Algorithm 1) over n particles.
+ *
+ * x, y, z, h : device, float32 [n], particle positions and smoothing lengths.
+ *              Read during the call only (the tree keeps its own copy).
+ * n          : 0 <= n < 2^31.
+ * bucket_size: s >= 1, the maximum number of particles in a leaf (Table 1).
+ * alpha      : fraction of s below which a sub-cell counts as underfull
+ *              (Table 1, Eq. 4); the paper's default is 0.5.
+ * beta       : the largest accepted ratio of underfull sub-cells (Eq. 4);
+ *              default 0.5.
+ * alloc      : allocator for internal buffers, or NULL.
+ * stream     : cudaStream_t.
+ * out        : host, receives the tree.  If *out already holds a tree from
+ *              an earlier btree_build, it is rebuilt in place and its device
+ *              buffers are reused when large enough.
+ *
+ * Readings of the paper (Sec. 3.1):
+ *  - b = smallest integer >= 2 with b^3 s >= count (Eq. 1 in integers);
+ *  - a sub-cell coordinate is clamp(floor(((x - lo)/(hi - lo)) * b), 0, b-1)
+ *    in binary64, 0 in a dimension with hi == lo (Eq. 2); id = c1 + c2 b +
+ *    c3 b^2 (Eq. 3);
+ *  - b is halved (b <- max(2, floor(b/2))) while #{j : n_j <= alpha s} >
+ *    beta b^3 and b > 2 (Eq. 4, the prose's "r larger than beta");
+ *  - sub-cell boxes: w = (hi-lo)/b, lo' = lo + c w, hi' = lo + (c+1) w
+ *    (hi' = hi for c = b-1); the root box is the inputs' bounding box;
+ *  - a cell with more than s particles stays a leaf at depth 32, or when
+ *    all its particles fall into one sub-cell whose box equals its own.
+ *
+ * Synchronises `stream` a few times (once per level of cells with more than
+ * 256 particles) to size the next level; returns when the tree is complete.
+ * Errors: BT_ERR_ARG (NULL pointer, n < 0, s < 1, alpha/beta not finite),
+ * BT_ERR_NONFINITE (a NaN/Inf coordinate or h, or h < 0), BT_ERR_OOM,
+ * BT_ERR_CUDA.  Warning: BT_WARN_OVERSIZED_LEAF.
+ */
+int btree_build(const float *x, const float *y, const float *z, const float *h,
+                int64_t n, int bucket_size, double alpha, double beta,
+                const bt_allocator *alloc, void *stream, btree_t **out);
+
+/*
+ * btree_find_neighbors -- FindNeighbors (Algorithm 2) for every particle.
+ *
+ * N(i) = { j != i : D(i,j) < (2 h_i)^2 } (strict, binary64, see above);
+ * the paper's Algorithm 2 writes "<=", its prose "less than"; the strict form
+ * is used.
+ * ngmax     : >= 1, row length of `neighbors`.
+ * neighbors : device, int32 [n * ngmax], row-major by ORIGINAL particle index:
+ *             row i holds the min(|N(i)|, ngmax) smallest j of N(i) in
+ *             ascending order; entries past that are not written.
+ * counts    : device, int32 [n], counts[i] = |N(i)| (uncapped).
+ * Asynchronous on `stream`.  Returns BT_OK on launch; device-detected
+ * conditions (a count above ngmax) are reported by btree_status.
+ */
+int btree_find_neighbors(const btree_t *t, int ngmax, int32_t *neighbors,
+                         int32_t *counts, void *stream);
+
+/*
+ * btree_find_neighbors_density -- FindNeighbors fused with the SPH density.
+ *
+ * As btree_find_neighbors, and in the same pass
+ *   rho[i] = m_i W(0, h_i) + sum_{j in N(i)} m_j W(r_ij, h_i)
+ * over the UNCAPPED set N(i), with the M4 cubic spline
+ *   W(r,h) = (1/(pi h^3)) {1 - 1.5 q^2 + 0.75 q^3 (0 <= q < 1);
+ *                          0.25 (2-q)^3 (1 <= q < 2); 0 (q >= 2)},  q = r/h,
+ * accumulated in float32 in a fixed order (deterministic).
+ * m   : device, float32 [n] masses.   rho : device, float32 [n].
+ */
+int btree_find_neighbors_density(const btree_t *t, const float *m, int ngmax,
+                                 int32_t *neighbors, int32_t *counts,
+                                 float *rho, void *stream);
+
+/*
+ * sph_density -- the density sum above, computed from existing lists.
+ *
+ * Uses the first min(counts[i], ngmax) entries of row i (so rows truncated
+ * by ngmax give a partial sum) and the positions and h the tree was built
+ * from.  m, neighbors, counts: device inputs; rho: device float32 [n].
+ */
+int sph_density(const btree_t *t, const float *m, const int32_t *neighbors,
+                const int32_t *counts, int ngmax, float *rho, void *stream);
+
+/* Reads (synchronising `stream`) and clears the tree's device status word:
+ * *out receives the most severe pending condition (BT_OK if none). */
+int btree_status(btree_t *t, void *stream, int *out);
+
+/* Fills *info (host).  Cheap; no device work. */
+int btree_get_info(const btree_t *t, bt_info *info);
+
+/*
+ * btree_export -- copy the tree to host memory (for inspection and tests).
+ * Any pointer may be NULL to skip that array.  Sizes come from bt_info.
+ *  node_lo, node_hi : host double [num_nodes*3] box of each internal node
+ *  node_b           : host int32 [num_nodes]  branching factor (0 = a cell
+ *                     with more than s particles that stayed a leaf)
+ *  node_depth       : host int32 [num_nodes]
+ *  node_start,count : host int32 [num_nodes]  particle range in tree order
+ *  node_slot0       : host int32 [num_nodes]  first sub-cell in `slot_*`
+ *  slot_start,count : host int32 [num_slots]  particle range of a sub-cell
+ *  slot_child       : host int32 [num_slots]  internal node id, or -1 (leaf)
+ *  order            : host int32 [n]          original index at each tree
+ *                     position
+ * Node 0 is the root.  Synchronises `stream`.
+ */
+int btree_export(const btree_t *t, void *stream, double *node_lo,
+                 double *node_hi, int32_t *node_b, int32_t *node_depth,
+                 int32_t *node_start, int32_t *node_count, int32_t *node_slot0,
+                 int32_t *slot_start, int32_t *slot_count, int32_t *slot_child,
+                 int32_t *order);
+
+/* Stream-ordered release of the tree and its buffers.  NULL is ignored. */
+void btree_free(btree_t *t);
+
+/* Static text for a status code. */
+const char *btree_strerror(int status);
+
+/* Library version string. */
+const char *btree_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BTREE_GB300_H */

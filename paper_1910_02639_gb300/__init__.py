@@ -1,0 +1,244 @@
+"""GB300 b-tree neighbour search (arXiv:1910.02639) -- Python binding.
+
+A thin ctypes layer over the C ABI of ``libbtree.so`` (``include/btree.h``):
+the same function names, argument marshalling only.  Every step of the build,
+the search and the density sum runs in the library's CUDA kernels; there is
+no CPU fallback.  Importing the package does not load the library; the first
+call does, and raises if it was not built (``python -m
+paper_1910_02639_gb300.build_ext`` or ``__graft_entry__.build()``).
+
+Tensors are PyTorch CUDA tensors (device memory and streams only):
+positions and smoothing lengths float32 [n], contiguous.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = [
+    "BtreeError", "Tree", "btree_build", "btree_find_neighbors",
+    "btree_find_neighbors_density", "sph_density", "btree_status", "btree_get_info",
+    "btree_export", "btree_free", "btree_strerror", "btree_version", "library_path",
+    "BT_OK", "BT_WARN_NGMAX", "BT_WARN_OVERSIZED_LEAF",
+]
+
+BT_OK = 0
+BT_ERR_ARG = -1
+BT_ERR_OOM = -2
+BT_ERR_CUDA = -3
+BT_ERR_TIMEOUT = -4
+BT_ERR_NONFINITE = -5
+BT_ERR_CAPACITY = -6
+BT_WARN_NGMAX = 1
+BT_WARN_OVERSIZED_LEAF = 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libbtree.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+class BtreeError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {btree_strerror(status)} ({status})")
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("bucket_size", ctypes.c_int32),
+                ("max_depth", ctypes.c_int32), ("num_nodes", ctypes.c_int64),
+                ("num_slots", ctypes.c_int64), ("num_groups", ctypes.c_int64),
+                ("root_b", ctypes.c_int32), ("num_oversized", ctypes.c_int32),
+                ("build_ms", ctypes.c_double)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(
+                f"{_LIB_PATH} is missing: build the CUDA library first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(_LIB_PATH)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        lib.btree_build.restype = ctypes.c_int
+        lib.btree_build.argtypes = [vp, vp, vp, vp, i64, ctypes.c_int, dbl, dbl, vp, vp,
+                                    ctypes.POINTER(vp)]
+        lib.btree_find_neighbors.restype = ctypes.c_int
+        lib.btree_find_neighbors.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+        lib.btree_find_neighbors_density.restype = ctypes.c_int
+        lib.btree_find_neighbors_density.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp]
+        lib.sph_density.restype = ctypes.c_int
+        lib.sph_density.argtypes = [vp, vp, vp, vp, ctypes.c_int, vp, vp]
+        lib.btree_status.restype = ctypes.c_int
+        lib.btree_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int)]
+        lib.btree_get_info.restype = ctypes.c_int
+        lib.btree_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
+        lib.btree_export.restype = ctypes.c_int
+        lib.btree_export.argtypes = [vp, vp] + [vp] * 11
+        lib.btree_free.restype = None
+        lib.btree_free.argtypes = [vp]
+        lib.btree_strerror.restype = ctypes.c_char_p
+        lib.btree_strerror.argtypes = [ctypes.c_int]
+        lib.btree_version.restype = ctypes.c_char_p
+        lib.btree_version.argtypes = []
+        _lib = lib
+        return lib
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(t, dtype, what, numel=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{what} has {t.numel()} elements, needs {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(status: int, what: str) -> int:
+    if status < 0:
+        raise BtreeError(status, what)
+    return status
+
+
+class Tree:
+    """Owns one btree_t.  Keeps the last build status in ``status``."""
+
+    def __init__(self):
+        self._ptr = ctypes.c_void_p(None)
+        self.status = BT_OK
+        self.n = 0
+
+    @property
+    def handle(self):
+        return self._ptr
+
+    def free(self):
+        if self._ptr and self._ptr.value:
+            _load().btree_free(self._ptr)
+        self._ptr = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        return btree_get_info(self)
+
+
+def btree_build(x, y, z, h, bucket_size: int = 16, alpha: float = 0.5, beta: float = 0.5,
+                stream=None, tree: Tree | None = None) -> Tree:
+    """BuildTree (Algorithm 1).  Rebuilds `tree` in place when given."""
+    import torch
+    lib = _load()
+    n = int(x.numel())
+    ptrs = [_dptr(a, torch.float32, nm, n) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (h, "h"))]
+    t = tree if tree is not None else Tree()
+    st = lib.btree_build(*ptrs, n, int(bucket_size), float(alpha), float(beta), None,
+                         ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(t._ptr))
+    _check(st, "btree_build")
+    t.status = st
+    t.n = n
+    return t
+
+
+def btree_find_neighbors(tree: Tree, ngmax: int, neighbors, counts, stream=None) -> int:
+    """FindNeighbors (Algorithm 2): rows ascending by original index, capped."""
+    import torch
+    n = tree.n
+    st = _load().btree_find_neighbors(
+        tree.handle, int(ngmax), _dptr(neighbors, torch.int32, "neighbors", n * ngmax),
+        _dptr(counts, torch.int32, "counts", n), ctypes.c_void_p(_stream_ptr(stream)))
+    return _check(st, "btree_find_neighbors")
+
+
+def btree_find_neighbors_density(tree: Tree, m, ngmax: int, neighbors, counts, rho,
+                                 stream=None) -> int:
+    """FindNeighbors fused with the M4 SPH density over the uncapped sets."""
+    import torch
+    n = tree.n
+    st = _load().btree_find_neighbors_density(
+        tree.handle, _dptr(m, torch.float32, "m", n), int(ngmax),
+        _dptr(neighbors, torch.int32, "neighbors", n * ngmax),
+        _dptr(counts, torch.int32, "counts", n), _dptr(rho, torch.float32, "rho", n),
+        ctypes.c_void_p(_stream_ptr(stream)))
+    return _check(st, "btree_find_neighbors_density")
+
+
+def sph_density(tree: Tree, m, neighbors, counts, ngmax: int, rho, stream=None) -> int:
+    """M4 density from existing rows (first min(count, ngmax) entries)."""
+    import torch
+    n = tree.n
+    st = _load().sph_density(
+        tree.handle, _dptr(m, torch.float32, "m", n),
+        _dptr(neighbors, torch.int32, "neighbors", n * ngmax),
+        _dptr(counts, torch.int32, "counts", n), int(ngmax),
+        _dptr(rho, torch.float32, "rho", n), ctypes.c_void_p(_stream_ptr(stream)))
+    return _check(st, "sph_density")
+
+
+def btree_status(tree: Tree, stream=None) -> int:
+    out = ctypes.c_int(0)
+    _check(_load().btree_status(tree.handle, ctypes.c_void_p(_stream_ptr(stream)),
+                                ctypes.byref(out)), "btree_status")
+    return int(out.value)
+
+
+def btree_get_info(tree: Tree) -> dict:
+    info = _Info()
+    _check(_load().btree_get_info(tree.handle, ctypes.byref(info)), "btree_get_info")
+    return {k: getattr(info, k) for k, _ in _Info._fields_}
+
+
+def btree_export(tree: Tree, stream=None) -> dict:
+    """Copy the tree to host numpy arrays (node table, sub-cells, order)."""
+    import numpy as np
+    info = btree_get_info(tree)
+    nn, ns, n = info["num_nodes"], info["num_slots"], info["n"]
+    out = dict(lo=np.zeros((nn, 3)), hi=np.zeros((nn, 3)), b=np.zeros(nn, np.int32),
+               depth=np.zeros(nn, np.int32), start=np.zeros(nn, np.int32),
+               count=np.zeros(nn, np.int32), slot0=np.zeros(nn, np.int32),
+               slot_start=np.zeros(ns, np.int32), slot_count=np.zeros(ns, np.int32),
+               slot_child=np.zeros(ns, np.int32), order=np.zeros(n, np.int32))
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    st = _load().btree_export(tree.handle, ctypes.c_void_p(_stream_ptr(stream)),
+                              p(out["lo"]), p(out["hi"]), p(out["b"]), p(out["depth"]),
+                              p(out["start"]), p(out["count"]), p(out["slot0"]),
+                              p(out["slot_start"]), p(out["slot_count"]),
+                              p(out["slot_child"]), p(out["order"]))
+    _check(st, "btree_export")
+    return out
+
+
+def btree_free(tree: Tree) -> None:
+    tree.free()
+
+
+def btree_strerror(status: int) -> str:
+    return _load().btree_strerror(int(status)).decode()
+
+
+def btree_version() -> str:
+    return _load().btree_version().decode()

@@ -1,0 +1,868 @@
+// bt_build.cu -- BuildTree (Algorithm 1 of arXiv:1910.02639) on the GPU.
+//
+// Level-synchronous for cells with more than kSmallCap particles ("big"
+// cells): one pass per candidate branching factor computes every particle's
+// sub-cell (Eqs. 2-3) and a global histogram n_j; one block per cell applies
+// the ratio test (Eq. 4) and halves b when it fails; an exclusive scan of the
+// accepted histograms places the sub-cells; a scatter moves each particle to
+// its sub-cell.  Cells of at most kSmallCap particles are built to the bottom
+// by one warp each, entirely in shared memory (depth-first, explicit stack).
+//
+// Particle records are float4 (x, y, z, original index as int bits) plus a
+// float h, in "tree order" once final: the particles of every cell, and so of
+// every sub-tree, occupy one contiguous range, sub-cells in id order.
+#include "bt_internal.cuh"
+#include "bt_build.cuh"
+
+#include <cfloat>
+
+namespace bt {
+
+// ------------------------------------------------------------------ bbox
+__global__ void __launch_bounds__(256) k_bbox(const float *__restrict__ x,
+                                              const float *__restrict__ y,
+                                              const float *__restrict__ z,
+                                              const float *__restrict__ h, int n,
+                                              Counters *ctr)
+{
+    float mn0 = FLT_MAX, mn1 = FLT_MAX, mn2 = FLT_MAX;
+    float mx0 = -FLT_MAX, mx1 = -FLT_MAX, mx2 = -FLT_MAX;
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float a = x[i], b = y[i], c = z[i], hh = h[i];
+        bad |= !isfinite(a) || !isfinite(b) || !isfinite(c) || !isfinite(hh) || !(hh >= 0.0f);
+        mn0 = fminf(mn0, a); mx0 = fmaxf(mx0, a);
+        mn1 = fminf(mn1, b); mx1 = fmaxf(mx1, b);
+        mn2 = fminf(mn2, c); mx2 = fmaxf(mx2, c);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mn0 = fminf(mn0, __shfl_xor_sync(~0u, mn0, o));
+        mn1 = fminf(mn1, __shfl_xor_sync(~0u, mn1, o));
+        mn2 = fminf(mn2, __shfl_xor_sync(~0u, mn2, o));
+        mx0 = fmaxf(mx0, __shfl_xor_sync(~0u, mx0, o));
+        mx1 = fmaxf(mx1, __shfl_xor_sync(~0u, mx1, o));
+        mx2 = fmaxf(mx2, __shfl_xor_sync(~0u, mx2, o));
+    }
+    bad = __any_sync(~0u, bad);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&ctr->bbox[0], float_to_ordered(mn0));
+        atomicMin(&ctr->bbox[1], float_to_ordered(mn1));
+        atomicMin(&ctr->bbox[2], float_to_ordered(mn2));
+        atomicMax(&ctr->bbox[3], float_to_ordered(mx0));
+        atomicMax(&ctr->bbox[4], float_to_ordered(mx1));
+        atomicMax(&ctr->bbox[5], float_to_ordered(mx2));
+        if (bad) atomicOr(&ctr->status, kStNonfinite);
+    }
+}
+
+// Root node from the bounding box (one thread).
+__global__ void k_root(TreeDev T, int n)
+{
+    Counters *ctr = T.ctr;
+    NodeGeom g;
+    for (int l = 0; l < 3; l++) {
+        double lo = (double)ordered_to_float(ctr->bbox[l]);
+        double hi = (double)ordered_to_float(ctr->bbox[3 + l]);
+        if (n == 0) { lo = 0.0; hi = 0.0; }
+        g.lo[l] = lo == 0.0 ? 0.0 : lo;  // canonical +0
+        g.hi[l] = hi == 0.0 ? 0.0 : hi;
+    }
+    g.start = 0;
+    g.count = n;
+    g.depth = 0;
+    g.pad = 0;
+    T.geom[0] = g;
+    NodeWalk w;
+    make_walk(g, 0, 0, w);
+    w.b = 0;  // a leaf until split
+    T.walk[0] = w;
+    ctr->nnodes = 1;
+}
+
+// Root with n <= s: copy the input to tree order unchanged; one or more groups.
+__global__ void k_root_leaf(TreeDev T, const float *__restrict__ x, const float *__restrict__ y,
+                            const float *__restrict__ z, const float *__restrict__ h, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        T.spos[i] = make_float4(x[i], y[i], z[i], __int_as_float(i));
+        T.sh[i] = h[i];
+        T.inv[i] = i;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int ng = (n + kGroupMax - 1) / kGroupMax;
+        for (int q = 0; q < ng; q++)
+            T.groups[q] = make_int2(q * kGroupMax, min(kGroupMax, n - q * kGroupMax));
+        T.ctr->ngroups = ng;
+    }
+}
+
+// ------------------------------------------------------------------ big cells
+__global__ void k_big_setup(TreeDev T, BigCell *big, const int *ids, int nb)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    int node = ids[i];
+    const NodeGeom &g = T.geom[node];
+    int b0 = branching_factor(g.count, T.s);
+    BigCell c;
+    c.node = node;
+    c.b0 = b0;
+    c.b = b0;
+    c.hist_base = b0 * b0 * b0;  // sizes, scanned next
+    c.chunk_base = (g.count + kBigChunk - 1) / kBigChunk;
+    c.state = 0;
+    c.slot0 = 0;
+    c.pad = 0;
+    big[i] = c;
+}
+
+// One block: exclusive scans of hist sizes and chunk counts over nb cells.
+__global__ void __launch_bounds__(1024) k_big_scan(BigCell *big, int nb, Counters *ctr)
+{
+    __shared__ long long sh_h[1024], sh_c[1024];
+    __shared__ long long carry_h, carry_c;
+    if (threadIdx.x == 0) { carry_h = 0; carry_c = 0; }
+    __syncthreads();
+    for (int base = 0; base < nb; base += 1024) {
+        int i = base + threadIdx.x;
+        long long vh = i < nb ? big[i].hist_base : 0;
+        long long vc = i < nb ? big[i].chunk_base : 0;
+        sh_h[threadIdx.x] = vh;
+        sh_c[threadIdx.x] = vc;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            long long ah = threadIdx.x >= o ? sh_h[threadIdx.x - o] : 0;
+            long long ac = threadIdx.x >= o ? sh_c[threadIdx.x - o] : 0;
+            __syncthreads();
+            sh_h[threadIdx.x] += ah;
+            sh_c[threadIdx.x] += ac;
+            __syncthreads();
+        }
+        if (i < nb) {
+            big[i].hist_base = (int)(carry_h + sh_h[threadIdx.x] - vh);
+            big[i].chunk_base = (int)(carry_c + sh_c[threadIdx.x] - vc);
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) {
+            carry_h += sh_h[1023];
+            carry_c += sh_c[1023];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        ctr->hist_total = (int)min(carry_h, (long long)INT_MAX);
+        ctr->chunk_total = (int)carry_c;
+        if (carry_h > INT_MAX) atomicOr(&ctr->status, kStCapBig);
+    }
+}
+
+__device__ __forceinline__ int find_cell_by_chunk(const BigCell *big, int nb, int chunk)
+{
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (big[mid].chunk_base <= chunk) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_cell_by_hist(const BigCell *big, int nb, int e)
+{
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (big[mid].hist_base <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per-block walk parameters of the block's cell for its current b.
+__device__ __forceinline__ void block_cell_params(const TreeDev &T, const BigCell &c,
+                                                  NodeGeom &g, NodeWalk &w, bool &ok)
+{
+    __shared__ NodeGeom s_g;
+    __shared__ NodeWalk s_w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_g = T.geom[c.node];
+        make_walk(s_g, c.b, 0, s_w);
+    }
+    __syncthreads();
+    g = s_g;
+    w = s_w;
+    ok = true;
+}
+
+__device__ __forceinline__ int sub_cell_id(const float4 &p, const NodeWalk &w, const NodeGeom &g, int b)
+{
+    int c0 = coord_fast(p.x, w, g, 0, b);
+    int c1 = coord_fast(p.y, w, g, 1, b);
+    int c2 = coord_fast(p.z, w, g, 2, b);
+    return c0 + b * (c1 + b * c2);
+}
+
+// Histogram pass of one candidate b for every pending big cell.
+__global__ void __launch_bounds__(256) k_big_hist(TreeDev T, const BigCell *big, int nb,
+                                                  Src src, int *hist)
+{
+    const int total = T.ctr->chunk_total;
+    for (int chunk = blockIdx.x; chunk < total; chunk += gridDim.x) {
+        int ci = find_cell_by_chunk(big, nb, chunk);
+        BigCell c = big[ci];
+        if (c.state != 0) continue;  // uniform across the block
+        NodeGeom g;
+        NodeWalk w;
+        bool ok;
+        block_cell_params(T, c, g, w, ok);
+        int p0 = g.start + (chunk - c.chunk_base) * kBigChunk;
+        int p1 = min(p0 + kBigChunk, g.start + g.count);
+        int *hc = hist + c.hist_base;
+        for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+            float4 r = src.load_pos(p);
+            atomicAdd(&hc[sub_cell_id(r, w, g, c.b)], 1);
+        }
+    }
+}
+
+// Ratio test (Eq. 4), one block per big cell.
+__global__ void __launch_bounds__(256) k_big_ratio(BigCell *big, int *hist, int na, double beta,
+                                                   Counters *ctr)
+{
+    BigCell &c = big[blockIdx.x];
+    if (c.state != 0) return;
+    const int b = c.b;
+    const int ncell = b * b * b;
+    const int *hc = hist + c.hist_base;
+    int u = 0;
+    for (int j = threadIdx.x; j < ncell; j += blockDim.x) u += hc[j] <= na;
+    __shared__ int s_u[8];
+    __shared__ int s_halve;
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(~0u, u, o);
+    if ((threadIdx.x & 31) == 0) s_u[threadIdx.x >> 5] = u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) tot += s_u[k];
+        bool halve = ((double)tot > __dmul_rn(beta, (double)ncell)) && b > 2;
+        s_halve = halve;
+        if (halve) {
+            c.b = max(2, b / 2);
+            ctr->again = 1;
+        } else {
+            c.state = 1;
+        }
+    }
+    __syncthreads();
+    if (s_halve) {
+        int *hw = hist + c.hist_base;
+        const int n0 = c.b0 * c.b0 * c.b0;
+        for (int j = threadIdx.x; j < n0; j += blockDim.x) hw[j] = 0;
+    }
+}
+
+// After acceptance: no-progress guard, walk parameters, slot placement.
+__global__ void __launch_bounds__(256) k_big_finish(TreeDev T, BigCell *big, const int *hist,
+                                                    int slot_level_base)
+{
+    BigCell &c = big[blockIdx.x];
+    const int b = c.b;
+    const int ncell = b * b * b;
+    const int *hc = hist + c.hist_base;
+    int nonempty = 0, last = -1;
+    for (int j = threadIdx.x; j < ncell; j += blockDim.x)
+        if (hc[j] > 0) { nonempty++; last = j; }
+    __shared__ int s_ne[8], s_last[8];
+    for (int o = 16; o > 0; o >>= 1) {
+        nonempty += __shfl_xor_sync(~0u, nonempty, o);
+        last = max(last, __shfl_xor_sync(~0u, last, o));
+    }
+    if ((threadIdx.x & 31) == 0) { s_ne[threadIdx.x >> 5] = nonempty; s_last[threadIdx.x >> 5] = last; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    int ne = 0, lj = -1;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) { ne += s_ne[k]; lj = max(lj, s_last[k]); }
+    const NodeGeom g = T.geom[c.node];
+    bool leaf = false;
+    if (ne == 1) {
+        int cc[3] = {lj % b, (lj / b) % b, lj / (b * b)};
+        bool same = true;
+        for (int l = 0; l < 3; l++) {
+            double clo, chi;
+            child_bounds(g.lo[l], g.hi[l], b, cc[l], clo, chi);
+            if (clo != g.lo[l] || chi != g.hi[l]) same = false;
+        }
+        leaf = same;
+    }
+    if (leaf) {
+        c.state = 2;
+        NodeWalk w;
+        make_walk(g, 0, 0, w);
+        w.b = 0;
+        T.walk[c.node] = w;
+        atomicAdd(&T.ctr->noversized, 1);
+        atomicOr(&T.ctr->status, kStOversized);
+        int ng = (g.count + kGroupMax - 1) / kGroupMax;
+        int g0 = atomicAdd(&T.ctr->ngroups, ng);
+        for (int q = 0; q < ng; q++)
+            if (g0 + q < T.cap_groups)
+                T.groups[g0 + q] = make_int2(g.start + q * kGroupMax, min(kGroupMax, g.count - q * kGroupMax));
+        if (g0 + ng > T.cap_groups) atomicOr(&T.ctr->status, kStCapGroups);
+        return;
+    }
+    c.slot0 = slot_level_base + c.hist_base;
+    NodeWalk w;
+    make_walk(g, b, c.slot0, w);
+    T.walk[c.node] = w;
+    atomicMax(&T.ctr->max_depth, g.depth + 1);
+}
+
+// Emit the sub-cells of every accepted big cell: slots, child nodes, queues,
+// leaf groups; cursor[e] = first tree position of sub-cell e.
+__global__ void __launch_bounds__(256) k_big_emit(TreeDev T, const BigCell *big, int nb,
+                                                  const int *hist, const int *hoff, int *cursor,
+                                                  int dst_buf, int *next_big, SmallItem *small)
+{
+    const int total = T.ctr->hist_total;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        int ci = find_cell_by_hist(big, nb, e);
+        const BigCell c = big[ci];
+        if (c.state != 1) continue;
+        const int b = c.b;
+        const int j = e - c.hist_base;
+        if (j >= b * b * b) continue;
+        const NodeGeom &g = T.geom[c.node];
+        const int cnt = hist[e];
+        const int start = g.start + (hoff[e] - hoff[c.hist_base]);
+        cursor[e] = start;
+        const int depth = g.depth + 1;
+        int child = -1;
+        if (cnt > T.s && depth < kDepthMax) {
+            child = atomicAdd(&T.ctr->nnodes, 1);
+            if (child >= T.cap_nodes) {
+                atomicOr(&T.ctr->status, kStCapNodes);
+                child = -1;
+            } else {
+                NodeGeom cg;
+                int cc[3] = {j % b, (j / b) % b, j / (b * b)};
+                for (int l = 0; l < 3; l++) child_bounds(g.lo[l], g.hi[l], b, cc[l], cg.lo[l], cg.hi[l]);
+                cg.start = start;
+                cg.count = cnt;
+                cg.depth = depth;
+                cg.pad = 0;
+                T.geom[child] = cg;
+                if (cnt > kSmallCap) {
+                    next_big[atomicAdd(&T.ctr->nbig_next, 1)] = child;
+                } else {
+                    int k = atomicAdd(&T.ctr->nsmall, 1);
+                    if (k < T.cap_small) small[k] = SmallItem{child, dst_buf};
+                    else atomicOr(&T.ctr->status, kStCapSmall);
+                }
+            }
+        } else if (cnt > 0) {
+            if (cnt > T.s) {
+                atomicAdd(&T.ctr->noversized, 1);
+                atomicOr(&T.ctr->status, kStOversized);
+            }
+            int ng = (cnt + kGroupMax - 1) / kGroupMax;
+            int g0 = atomicAdd(&T.ctr->ngroups, ng);
+            for (int q = 0; q < ng; q++)
+                if (g0 + q < T.cap_groups)
+                    T.groups[g0 + q] = make_int2(start + q * kGroupMax, min(kGroupMax, cnt - q * kGroupMax));
+            if (g0 + ng > T.cap_groups) atomicOr(&T.ctr->status, kStCapGroups);
+        }
+        T.slots[c.slot0 + j] = Slot{start, cnt, child, 0};
+    }
+}
+
+// Move every particle of an accepted big cell to its sub-cell.  Leaf
+// sub-cells are final: they go straight to tree order; others to the
+// working buffer `dst` for the next level / the warp builder.
+__global__ void __launch_bounds__(256) k_big_scatter(TreeDev T, const BigCell *big, int nb, Src src,
+                                                     int *cursor, float4 *dst_pos, float *dst_h)
+{
+    const int total = T.ctr->chunk_total;
+    for (int chunk = blockIdx.x; chunk < total; chunk += gridDim.x) {
+        int ci = find_cell_by_chunk(big, nb, chunk);
+        BigCell c = big[ci];
+        NodeGeom g;
+        NodeWalk w;
+        bool ok;
+        block_cell_params(T, c, g, w, ok);
+        int p0 = g.start + (chunk - c.chunk_base) * kBigChunk;
+        int p1 = min(p0 + kBigChunk, g.start + g.count);
+        for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+            float4 r;
+            float hh;
+            src.load(p, r, hh);
+            if (c.state == 2) {  // stayed a leaf: final where it is
+                T.spos[p] = r;
+                T.sh[p] = hh;
+                T.inv[__float_as_int(r.w)] = p;
+                continue;
+            }
+            int j = sub_cell_id(r, w, g, c.b);
+            int pos = atomicAdd(&cursor[c.hist_base + j], 1);
+            if (T.slots[c.slot0 + j].child < 0) {
+                T.spos[pos] = r;
+                T.sh[pos] = hh;
+                T.inv[__float_as_int(r.w)] = pos;
+            } else {
+                dst_pos[pos] = r;
+                dst_h[pos] = hh;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ scan
+// Exclusive scan of int32 counts (sums fit in int32).
+constexpr int kScanTile = 4096;
+
+__global__ void __launch_bounds__(256) k_scan_tiles(const int *in, int n, int *tile_sum)
+{
+    int t0 = blockIdx.x * kScanTile;
+    int s = 0;
+    for (int i = t0 + threadIdx.x; i < min(t0 + kScanTile, n); i += blockDim.x) s += in[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(~0u, s, o);
+    __shared__ int ws[8];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int k = 0; k < 8; k++) t += ws[k];
+        tile_sum[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tile_sums(int *tile_sum, int ntiles)
+{
+    __shared__ int sh[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < ntiles; base += 1024) {
+        int i = base + threadIdx.x;
+        int v = i < ntiles ? tile_sum[i] : 0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            int a = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += a;
+            __syncthreads();
+        }
+        if (i < ntiles) tile_sum[i] = carry + sh[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += sh[1023];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scan_apply(const int *in, int n, const int *tile_off, int *out)
+{
+    // 256 threads x 16 items
+    __shared__ int ws[8];
+    int t0 = blockIdx.x * kScanTile;
+    int v[16];
+    int s = 0;
+    for (int k = 0; k < 16; k++) {
+        int i = t0 + threadIdx.x * 16 + k;
+        v[k] = i < n ? in[i] : 0;
+        s += v[k];
+    }
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        int a = __shfl_up_sync(~0u, incl, o);
+        if (lane >= o) incl += a;
+    }
+    if (lane == 31) ws[wid] = incl;
+    __syncthreads();
+    int woff = 0;
+    for (int k = 0; k < wid; k++) woff += ws[k];
+    int run = tile_off[blockIdx.x] + woff + incl - s;
+    for (int k = 0; k < 16; k++) {
+        int i = t0 + threadIdx.x * 16 + k;
+        if (i < n) out[i] = run;
+        run += v[k];
+    }
+}
+
+// ------------------------------------------------------------------ warp builder
+struct Frame {
+    double lo[3], hi[3];
+    int a, m, node, depth;
+    int b, slot0, next, emit;
+};
+
+constexpr int kSmallWarps = 4;
+constexpr int kHistMax = 512;  // >= b0^3 for any cell of <= kSmallCap particles
+
+struct SmallSmem {
+    float4 p[2][kSmallCap];
+    float h[2][kSmallCap];
+    short key[kSmallCap];
+    int hist[kHistMax];
+    int off[kHistMax];
+    Frame fr[kDepthMax + 2];
+    NodeWalk w;
+    int scal[4];
+};
+
+__device__ __forceinline__ int warp_sum(int v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(~0u, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void emit_groups(const TreeDev &T, int start, int cnt)
+{
+    int ng = (cnt + kGroupMax - 1) / kGroupMax;
+    int g0 = atomicAdd(&T.ctr->ngroups, ng);
+    for (int q = 0; q < ng; q++)
+        if (g0 + q < T.cap_groups)
+            T.groups[g0 + q] = make_int2(start + q * kGroupMax, min(kGroupMax, cnt - q * kGroupMax));
+    if (g0 + ng > T.cap_groups) atomicOr(&T.ctr->status, kStCapGroups);
+}
+
+// One warp builds the whole sub-tree of one cell of <= kSmallCap particles.
+__global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const SmallItem *items,
+                                                            int nitems, Src src0, Src src1,
+                                                            Src srcin, int na, double beta)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmallSmem &S = reinterpret_cast<SmallSmem *>(smem_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kSmallWarps + (threadIdx.x >> 5);
+    const int nw = gridDim.x * kSmallWarps;
+
+    for (int it = gw; it < nitems; it += nw) {
+        const SmallItem item = items[it];
+        const NodeGeom G = T.geom[item.node];
+        const int base = G.start, m0 = G.count;
+        const Src &src = item.src == 0 ? src0 : (item.src == 1 ? src1 : srcin);
+        for (int k = lane; k < m0; k += 32) {
+            float4 r;
+            float hh;
+            src.load(base + k, r, hh);
+            S.p[0][k] = r;
+            S.h[0][k] = hh;
+        }
+        if (lane == 0) {
+            Frame &f = S.fr[0];
+            for (int l = 0; l < 3; l++) { f.lo[l] = G.lo[l]; f.hi[l] = G.hi[l]; }
+            f.a = 0; f.m = m0; f.node = item.node; f.depth = G.depth;
+            f.b = 0; f.slot0 = 0; f.next = 0; f.emit = m0 > kGroupMax;
+            if (m0 <= kGroupMax) emit_groups(T, base, m0);
+        }
+        int sp = 1;
+        __syncwarp();
+        while (sp > 0) {
+            Frame &F = S.fr[sp - 1];
+            if (F.b == 0) {
+                // ---- split cell F (Algorithm 1, Steps 1-3)
+                const int a = F.a, m = F.m;
+                NodeGeom g;
+                for (int l = 0; l < 3; l++) { g.lo[l] = F.lo[l]; g.hi[l] = F.hi[l]; }
+                g.start = base + a; g.count = m; g.depth = F.depth; g.pad = 0;
+                int b = branching_factor(m, T.s);
+                for (;;) {
+                    if (lane == 0) make_walk(g, b, 0, S.w);
+                    __syncwarp();
+                    const NodeWalk w = S.w;
+                    const int ncell = b * b * b;
+                    for (int j = lane; j < ncell; j += 32) S.hist[j] = 0;
+                    __syncwarp();
+                    for (int k = lane; k < m; k += 32) {
+                        int j = sub_cell_id(S.p[0][a + k], w, g, b);
+                        S.key[a + k] = (short)j;
+                        atomicAdd(&S.hist[j], 1);
+                    }
+                    __syncwarp();
+                    int u = 0;
+                    for (int j = lane; j < ncell; j += 32) u += S.hist[j] <= na;
+                    u = warp_sum(u);
+                    if ((double)u > __dmul_rn(beta, (double)ncell) && b > 2) {
+                        b = max(2, b / 2);
+                        __syncwarp();
+                        continue;
+                    }
+                    break;
+                }
+                const int ncell = b * b * b;
+                // no-progress guard
+                int ne = 0, lj = -1;
+                for (int j = lane; j < ncell; j += 32)
+                    if (S.hist[j] > 0) { ne++; lj = j; }
+                ne = warp_sum(ne);
+                for (int o = 16; o > 0; o >>= 1) lj = max(lj, __shfl_xor_sync(~0u, lj, o));
+                bool leaf = false;
+                if (ne == 1) {
+                    int cc[3] = {lj % b, (lj / b) % b, lj / (b * b)};
+                    bool same = true;
+                    for (int l = 0; l < 3; l++) {
+                        double clo, chi;
+                        child_bounds(g.lo[l], g.hi[l], b, cc[l], clo, chi);
+                        if (clo != g.lo[l] || chi != g.hi[l]) same = false;
+                    }
+                    leaf = same;
+                }
+                if (leaf) {
+                    if (lane == 0) {
+                        NodeWalk w;
+                        make_walk(g, 0, 0, w);
+                        w.b = 0;
+                        T.walk[F.node] = w;
+                        atomicAdd(&T.ctr->noversized, 1);
+                        atomicOr(&T.ctr->status, kStOversized);
+                        if (F.emit) emit_groups(T, base + a, m);
+                    }
+                    sp--;
+                    __syncwarp();
+                    continue;
+                }
+                // exclusive scan of the histogram
+                {
+                    int carry = 0;
+                    for (int j0 = 0; j0 < ncell; j0 += 32) {
+                        int j = j0 + lane;
+                        int v = j < ncell ? S.hist[j] : 0;
+                        int incl = v;
+                        for (int o = 1; o < 32; o <<= 1) {
+                            int t = __shfl_up_sync(~0u, incl, o);
+                            if (lane >= o) incl += t;
+                        }
+                        if (j < ncell) S.off[j] = carry + incl - v;
+                        carry += __shfl_sync(~0u, incl, 31);
+                    }
+                }
+                int slot0 = 0;
+                if (lane == 0) {
+                    slot0 = atomicAdd(&T.ctr->nslots, ncell);
+                    if (slot0 + ncell > T.cap_slots) {
+                        atomicOr(&T.ctr->status, kStCapSlots);
+                        slot0 = -1;
+                    }
+                }
+                slot0 = __shfl_sync(~0u, slot0, 0);
+                __syncwarp();
+                if (slot0 < 0) {  // out of slot capacity: abandon this sub-tree (host rebuilds)
+                    sp = 0;
+                    break;
+                }
+                for (int j = lane; j < ncell; j += 32) {
+                    const int cnt = S.hist[j];
+                    const int start = base + a + S.off[j];
+                    const int depth = F.depth + 1;
+                    int child = -1;
+                    if (cnt > T.s && depth < kDepthMax) {
+                        child = atomicAdd(&T.ctr->nnodes, 1);
+                        if (child >= T.cap_nodes) {
+                            atomicOr(&T.ctr->status, kStCapNodes);
+                            child = -1;
+                        } else {
+                            NodeGeom cg;
+                            int cc[3] = {j % b, (j / b) % b, j / (b * b)};
+                            for (int l = 0; l < 3; l++)
+                                child_bounds(g.lo[l], g.hi[l], b, cc[l], cg.lo[l], cg.hi[l]);
+                            cg.start = start; cg.count = cnt; cg.depth = depth; cg.pad = 0;
+                            T.geom[child] = cg;
+                            if (F.emit && cnt <= kGroupMax) emit_groups(T, start, cnt);
+                        }
+                    } else if (cnt > 0) {
+                        if (cnt > T.s) {
+                            atomicAdd(&T.ctr->noversized, 1);
+                            atomicOr(&T.ctr->status, kStOversized);
+                        }
+                        if (F.emit) emit_groups(T, start, cnt);
+                    }
+                    T.slots[slot0 + j] = Slot{start, cnt, child, 0};
+                }
+                if (lane == 0) {
+                    NodeWalk w;
+                    make_walk(g, b, slot0, w);
+                    T.walk[F.node] = w;
+                    atomicMax(&T.ctr->max_depth, F.depth + 1);
+                }
+                // scatter within shared memory, then copy back
+                for (int j = lane; j < ncell; j += 32) S.hist[j] = S.off[j];
+                __syncwarp();
+                for (int k = lane; k < m; k += 32) {
+                    int j = S.key[a + k];
+                    int pos = atomicAdd(&S.hist[j], 1);
+                    S.p[1][a + pos] = S.p[0][a + k];
+                    S.h[1][a + pos] = S.h[0][a + k];
+                }
+                __syncwarp();
+                for (int k = lane; k < m; k += 32) {
+                    S.p[0][a + k] = S.p[1][a + k];
+                    S.h[0][a + k] = S.h[1][a + k];
+                }
+                if (lane == 0) { F.b = b; F.slot0 = slot0; F.next = 0; }
+                __syncwarp();
+            } else {
+                // ---- descend into the next internal sub-cell
+                const int ncell = F.b * F.b * F.b;
+                int found = -1;
+                while (F.next < ncell && found < 0) {
+                    int j = F.next + lane;
+                    bool isint = false;
+                    if (j < ncell) isint = T.slots[F.slot0 + j].child >= 0;
+                    unsigned bal = __ballot_sync(~0u, isint);
+                    if (bal) found = F.next + __ffs(bal) - 1;
+                    __syncwarp();
+                    if (lane == 0) F.next = bal ? found + 1 : F.next + 32;
+                    __syncwarp();
+                }
+                if (found < 0) {
+                    sp--;
+                    __syncwarp();
+                    continue;
+                }
+                if (lane == 0) {
+                    const Slot s = T.slots[F.slot0 + found];
+                    Frame &C = S.fr[sp];
+                    const int b = F.b;
+                    int cc[3] = {found % b, (found / b) % b, found / (b * b)};
+                    for (int l = 0; l < 3; l++) child_bounds(F.lo[l], F.hi[l], b, cc[l], C.lo[l], C.hi[l]);
+                    C.a = s.start - base; C.m = s.count; C.node = s.child; C.depth = F.depth + 1;
+                    C.b = 0; C.slot0 = 0; C.next = 0; C.emit = F.emit && s.count > kGroupMax;
+                }
+                sp++;
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+        for (int k = lane; k < m0; k += 32) {
+            float4 r = S.p[0][k];
+            T.spos[base + k] = r;
+            T.sh[base + k] = S.h[0][k];
+            T.inv[__float_as_int(r.w)] = base + k;
+        }
+        __syncwarp();
+    }
+}
+
+size_t small_smem_bytes() { return sizeof(SmallSmem) * kSmallWarps; }
+
+// ------------------------------------------------------------------ host side
+static inline int grid_for(long long work, int per_block, int max_blocks)
+{
+    long long g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+void launch_bbox(const float *x, const float *y, const float *z, const float *h, int n,
+                 Counters *ctr, int sms, cudaStream_t st)
+{
+    k_bbox<<<grid_for(n, 256 * 8, sms * 8), 256, 0, st>>>(x, y, z, h, n, ctr);
+}
+
+void launch_root(const TreeDev &T, int n, cudaStream_t st) { k_root<<<1, 1, 0, st>>>(T, n); }
+
+void launch_root_leaf(const TreeDev &T, const float *x, const float *y, const float *z,
+                      const float *h, int n, int sms, cudaStream_t st)
+{
+    k_root_leaf<<<grid_for(n, 256, sms * 4), 256, 0, st>>>(T, x, y, z, h, n);
+}
+
+void launch_big_setup(const TreeDev &T, BigCell *big, const int *ids, int nb, cudaStream_t st)
+{
+    k_big_setup<<<grid_for(nb, 256, 1 << 20), 256, 0, st>>>(T, big, ids, nb);
+    k_big_scan<<<1, 1024, 0, st>>>(big, nb, T.ctr);
+}
+
+void launch_big_hist(const TreeDev &T, const BigCell *big, int nb, int chunks, Src src, int *hist,
+                     int sms, cudaStream_t st)
+{
+    k_big_hist<<<grid_for(chunks, 1, sms * 8), 256, 0, st>>>(T, big, nb, src, hist);
+}
+
+void launch_big_ratio(BigCell *big, int nb, int *hist, int na, double beta, Counters *ctr,
+                      cudaStream_t st)
+{
+    k_big_ratio<<<nb, 256, 0, st>>>(big, hist, na, beta, ctr);
+}
+
+void launch_big_finish(const TreeDev &T, BigCell *big, int nb, const int *hist, int slot_level_base,
+                       cudaStream_t st)
+{
+    k_big_finish<<<nb, 256, 0, st>>>(T, big, hist, slot_level_base);
+}
+
+void launch_scan(const int *in, int n, int *tile_buf, int *out, cudaStream_t st)
+{
+    int ntiles = (n + kScanTile - 1) / kScanTile;
+    if (ntiles < 1) ntiles = 1;
+    k_scan_tiles<<<ntiles, 256, 0, st>>>(in, n, tile_buf);
+    k_scan_tile_sums<<<1, 1024, 0, st>>>(tile_buf, ntiles);
+    k_scan_apply<<<ntiles, 256, 0, st>>>(in, n, tile_buf, out);
+}
+
+int scan_tile_count(int n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+void launch_big_emit(const TreeDev &T, const BigCell *big, int nb, int hist_total, const int *hist,
+                     const int *hoff, int *cursor, int dst_buf, int *next_big, SmallItem *small,
+                     int sms, cudaStream_t st)
+{
+    k_big_emit<<<grid_for(hist_total, 256, sms * 16), 256, 0, st>>>(T, big, nb, hist, hoff, cursor,
+                                                                     dst_buf, next_big, small);
+}
+
+void launch_big_scatter(const TreeDev &T, const BigCell *big, int nb, int chunks, Src src,
+                        int *cursor, float4 *dst_pos, float *dst_h, int sms, cudaStream_t st)
+{
+    k_big_scatter<<<grid_for(chunks, 1, sms * 8), 256, 0, st>>>(T, big, nb, src, cursor, dst_pos,
+                                                                dst_h);
+}
+
+void launch_small(const TreeDev &T, const SmallItem *items, int nitems, Src src0, Src src1,
+                  Src srcin, int na, double beta, int sms, cudaStream_t st)
+{
+    if (nitems <= 0) return;
+    int blocks = grid_for(nitems, kSmallWarps, sms * 4);
+    k_small<<<blocks, 32 * kSmallWarps, small_smem_bytes(), st>>>(T, items, nitems, src0, src1,
+                                                                   srcin, na, beta);
+}
+
+cudaError_t build_init_attributes()
+{
+    return cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)small_smem_bytes());
+}
+
+__global__ void k_init_counters(Counters *ctr)
+{
+    Counters c = {};
+    for (int l = 0; l < 3; l++) {
+        c.bbox[l] = INT_MAX;
+        c.bbox[3 + l] = INT_MIN;
+    }
+    *ctr = c;
+}
+
+__global__ void k_set_int(int *p, int v) { *p = v; }
+
+// Queue the root for the warp builder (s < n <= kSmallCap) or the big-cell
+// levels (n > kSmallCap).
+__global__ void k_set_small_root(SmallItem *small, int *big_ids, int n, int s, Counters *ctr)
+{
+    if (n > s && n <= kSmallCap) {
+        small[0] = SmallItem{0, 2};
+        ctr->nsmall = 1;
+    } else if (n > kSmallCap) {
+        big_ids[0] = 0;
+    }
+}
+
+void launch_init_counters(Counters *ctr, cudaStream_t st) { k_init_counters<<<1, 1, 0, st>>>(ctr); }
+void launch_set_int(int *p, int v, cudaStream_t st) { k_set_int<<<1, 1, 0, st>>>(p, v); }
+void launch_set_small_root(SmallItem *small, int *big_ids, int n, int s, Counters *ctr,
+                           cudaStream_t st)
+{
+    k_set_small_root<<<1, 1, 0, st>>>(small, big_ids, n, s, ctr);
+}
+
+}  // namespace bt

@@ -1,0 +1,14 @@
+// bt_find.cuh -- launchers of the FindNeighbors and density kernels (bt_find.cu).
+#pragma once
+#include "bt_internal.cuh"
+
+namespace bt {
+
+cudaError_t launch_find(const TreeDev &T, int ngroups, int ngmax, int32_t *nbrs, int32_t *counts,
+                        const float *m, float *smass, float *rho, int sms, cudaStream_t st);
+cudaError_t launch_density(const TreeDev &T, const float *m, const int32_t *nbrs,
+                           const int32_t *counts, int ngmax, float *rho, int sms, cudaStream_t st);
+size_t find_smem_bytes();
+cudaError_t find_init_attributes();
+
+}  // namespace bt

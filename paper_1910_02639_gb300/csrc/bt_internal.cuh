@@ -1,0 +1,262 @@
+// bt_internal.cuh -- device data layout and geometry primitives shared by the
+// build, find and density kernels of the b-tree (arXiv:1910.02639).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/btree.h"
+
+namespace bt {
+
+constexpr int kDepthMax = 32;   // a cell at depth 32 is never split
+constexpr int kGroupMax = 32;   // particles per find work unit (one per lane)
+constexpr int kSmallCap = 256;  // cells up to this size are built by one warp in smem
+constexpr int kBigChunk = 4096; // particles per block in the per-level big-cell passes
+
+// Status bits accumulated on the device (reported by btree_status).
+enum : uint32_t {
+    kStNgmax = 1u << 0,
+    kStOversized = 1u << 1,
+    kStNonfinite = 1u << 2,
+    kStCapNodes = 1u << 3,
+    kStCapSlots = 1u << 4,
+    kStCapGroups = 1u << 5,
+    kStCapSmall = 1u << 6,
+    kStCapBig = 1u << 7,
+    kStWalk = 1u << 8,  // a find work unit fell back to a wider (still exact) path
+};
+
+// NodeWalk.flags
+enum : int {
+    kFlagLeaf = 1,         // a cell with > s particles that stayed a leaf
+    kFlagWide = 2,         // FP32 fast path unusable: build uses FP64, walk visits all cells
+    kFlagDegen0 = 4,       // zero width in dimension 0 (then 8, 16 for dims 1, 2)
+};
+
+// Exact binary64 box of an internal node plus its particle range (build side).
+struct __align__(16) NodeGeom {
+    double lo[3];
+    double hi[3];
+    int start, count, depth, pad;
+};
+
+// What the walk and the per-particle sub-cell computation read (48 B + range).
+struct __align__(16) NodeWalk {
+    float lo[3];     // fl32(lo)
+    float scale[3];  // fl32(b / (hi - lo)); 0 in a zero-width dimension
+    float cn[3];     // additive error bound of the FP32 sub-cell coordinate
+    int b;           // branching factor (0: unsplit)
+    int slot0;       // first sub-cell
+    int flags;
+    int start, count, pad0, pad1;
+};
+
+// One sub-cell: its particle range in tree order and the internal node it is,
+// or -1 for a leaf.  Sub-cells of a node are contiguous in id order, and so
+// are their particle ranges.
+struct __align__(16) Slot {
+    int start, count, child, pad;
+};
+
+// -------------------------------------------------------------------------
+// Eq. 2 in binary64, exactly as the definition: floor(((x-lo)/(hi-lo))*b),
+// clamped to [0, b-1].  Each operation is a correctly rounded intrinsic, so
+// no contraction or reassociation can change it.
+__device__ __forceinline__ int coord_fp64(float x, double lo, double hi, int b)
+{
+    double t = __ddiv_rn(__dsub_rn((double)x, lo), __dsub_rn(hi, lo));
+    double v = __dmul_rn(t, (double)b);
+    double f = floor(v);
+    if (!(f >= 0.0)) return 0;
+    if (f > (double)(b - 1)) return b - 1;
+    return (int)f;
+}
+
+// Eq. 2 with an FP32 fast path.  v32 = fl32(fl32(x - lo32) * scale32) differs
+// from the binary64 value v by at most E = 2^-22 (|v32| + |lo| s) +
+// 2^-147 (s + 1), s = b/(hi-lo) (three float roundings of relative size
+// 2^-24 on the value and on lo, plus underflow; cn holds the constant part
+// rounded up).  If v32 is farther than E from every integer, floor(v32) =
+// floor(v); otherwise the binary64 definition decides.
+__device__ __forceinline__ int coord_fast(float x, const NodeWalk &w, const NodeGeom &g,
+                                          int l, int b)
+{
+    if (w.flags & (kFlagDegen0 << l)) return 0;
+    if (!(w.flags & kFlagWide)) {
+        float v = __fmul_rn(__fsub_rn(x, w.lo[l]), w.scale[l]);
+        float av = fabsf(v);
+        if (av < 4194304.0f) {  // 2^22: fractional part exact
+            float e = __fmaf_ru(av, 0x1p-22f, w.cn[l]);
+            float k = floorf(v);
+            if (__fsub_rn(v, k) > e && __fsub_rn(k + 1.0f, v) > e) {
+                int c = (int)k;
+                return c < 0 ? 0 : (c > b - 1 ? b - 1 : c);
+            }
+        }
+    }
+    return coord_fp64(x, g.lo[l], g.hi[l], b);
+}
+
+// Conservative range of sub-cells [r0, r1] in one dimension whose cells may
+// hold a particle with coordinate in [ql, qh] (Eqs. 5-6 on an interval).
+// Rounded outward by the same error bound, so it always contains the exact
+// binary64 range; clamped like Eq. 2.
+__device__ __forceinline__ void walk_range(float ql, float qh, const NodeWalk &w, int l,
+                                           int &r0, int &r1)
+{
+    int b = w.b;
+    if (w.flags & (kFlagDegen0 << l)) { r0 = 0; r1 = 0; return; }
+    if (w.flags & kFlagWide) { r0 = 0; r1 = b - 1; return; }
+    // same operation sequence as coord_fast, so the same bound E applies
+    float vl = __fmul_rn(__fsub_rn(ql, w.lo[l]), w.scale[l]);
+    float vh = __fmul_rn(__fsub_rn(qh, w.lo[l]), w.scale[l]);
+    float el = __fmaf_ru(fabsf(vl), 0x1p-22f, w.cn[l]);
+    float eh = __fmaf_ru(fabsf(vh), 0x1p-22f, w.cn[l]);
+    float fl = floorf(__fsub_rd(vl, el));
+    float fh = floorf(__fadd_ru(vh, eh));
+    // clamp in float first (also maps NaN to the full range)
+    fl = fmaxf(fl, 0.0f);
+    fh = fminf(fh, (float)(b - 1));
+    if (!(fl <= (float)(b - 1))) fl = (float)(b - 1);
+    if (!(fh >= 0.0f)) fh = 0.0f;
+    r0 = (int)fl;
+    r1 = (int)fh;
+}
+
+// Fill the walk/coordinate parameters of a node with branching factor b.
+__device__ __forceinline__ void make_walk(const NodeGeom &g, int b, int slot0, NodeWalk &w)
+{
+    w.b = b;
+    w.slot0 = slot0;
+    w.flags = 0;
+    w.start = g.start;
+    w.count = g.count;
+    w.pad0 = w.pad1 = 0;
+    for (int l = 0; l < 3; l++) {
+        double width = __dsub_rn(g.hi[l], g.lo[l]);
+        w.lo[l] = __double2float_rn(g.lo[l]);
+        if (width == 0.0) {
+            w.flags |= (kFlagDegen0 << l);
+            w.scale[l] = 0.0f;
+            w.cn[l] = 0.0f;
+            continue;
+        }
+        double s = __ddiv_rn((double)b, width);
+        double alo = fabs(g.lo[l]);
+        if (!(s < 1e30) || !(alo < 1e30)) {
+            w.flags |= kFlagWide;
+            w.scale[l] = 0.0f;
+            w.cn[l] = 0.0f;
+            continue;
+        }
+        w.scale[l] = __double2float_rn(s);
+        double c = 0x1p-22 * (alo * s + 1.0) + 0x1p-147 * (s + 1.0);
+        w.cn[l] = __double2float_ru(c * (1.0 + 0x1p-40));
+    }
+}
+
+// Child box of sub-cell coordinate c in one dimension (Sec. 3.1 step 2,
+// equal-size sub-cells), binary64 in the oracle's operation order.
+__device__ __forceinline__ void child_bounds(double lo, double hi, int b, int c,
+                                             double &clo, double &chi)
+{
+    double w = __ddiv_rn(__dsub_rn(hi, lo), (double)b);
+    clo = __dadd_rn(lo, __dmul_rn((double)c, w));
+    chi = (c == b - 1) ? hi : __dadd_rn(lo, __dmul_rn((double)(c + 1), w));
+}
+
+// Eq. 1 in integers: smallest b >= 2 with b^3 s >= n.
+__device__ __host__ __forceinline__ int branching_factor(long long n, long long s)
+{
+    long long b = (long long)cbrt((double)n / (double)s);
+    if (b < 2) b = 2;
+    while (b > 2 && (b - 1) * (b - 1) * (b - 1) * s >= n) b--;
+    while (b * b * b * s < n) b++;
+    return (int)b;
+}
+
+// Order-preserving float <-> int map for atomicMin/atomicMax on floats.
+__device__ __forceinline__ int float_to_ordered(float f)
+{
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ordered_to_float(int i)
+{
+    return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff);
+}
+
+// Device-side counters of one build (one struct in device memory).
+struct Counters {
+    int nnodes;        // internal nodes allocated
+    int nslots;        // sub-cells allocated
+    int ngroups;       // find groups emitted
+    int nsmall;        // cells queued for the warp builder
+    int nbig_next;     // big cells queued for the next level
+    int again;         // some big cell halved b in the last ratio pass
+    int max_depth;
+    int noversized;
+    int bbox[6];       // ordered-int min x,y,z then max x,y,z
+    unsigned status;
+    int find_next;     // dynamic work counter of the find kernels
+    int hist_total;    // sum of b0^3 over this level's big cells
+    int chunk_total;   // blocks of kBigChunk particles over this level's big cells
+    int pad[2];
+};
+
+// Per big cell of the current level.
+struct BigCell {
+    int node;
+    int b0, b;
+    int hist_base;     // offset into the level histogram
+    int chunk_base;    // first kBigChunk block of this cell
+    int state;         // 0 pending, 1 accepted, 2 stays a leaf
+    int slot0;
+    int pad;
+};
+
+struct SmallItem {
+    int node;
+    int src;  // 0/1: working buffer holding its particles; 2: the input arrays
+};
+
+// Everything the kernels need to see of one tree.
+struct TreeDev {
+    int n;
+    int s;
+    NodeGeom *geom;
+    NodeWalk *walk;
+    Slot *slots;
+    int2 *groups;
+    float4 *spos;   // tree order: x, y, z, orig index (bits)
+    float *sh;      // tree order: h
+    int *inv;       // inverse permutation: tree position of original index
+    Counters *ctr;
+    int cap_nodes, cap_slots, cap_groups, cap_small;
+};
+
+// Load particle p of the level's source: the input arrays (root level) or a
+// working buffer.
+struct Src {
+    const float *x, *y, *z, *h;  // input arrays, or null
+    const float4 *pos;           // working buffer records
+    const float *ph;
+    __device__ __forceinline__ void load(int p, float4 &r, float &hh) const
+    {
+        if (x) {
+            r = make_float4(x[p], y[p], z[p], __int_as_float(p));
+            hh = h[p];
+        } else {
+            r = pos[p];
+            hh = ph[p];
+        }
+    }
+    __device__ __forceinline__ float4 load_pos(int p) const
+    {
+        if (x) return make_float4(x[p], y[p], z[p], __int_as_float(p));
+        return pos[p];
+    }
+};
+
+}  // namespace bt
