@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Benchmark of the b-tree neighbour search (arXiv:1910.02639) on GB300.
+
+One step = the whole hot path over one particle set: BuildTree (bounding box,
+per-level sub-cell histograms / ratio test / scan / scatter, warp-level
+sub-trees) + FindNeighbors fused with the M4 density (walk, gather, sort,
+test, ordered capped rows).  Default workload: the jittered lattice slab of
+1e7 particles (400 x 250 x 100, spacing 1, jitter +-0.1, h = 1.5, masses 1/N),
+bucket size 16, ngmax 256.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  `value` = neighbour pairs (sum of uncapped
+counts) per second over all ranks, inputs resident in HBM; `e2e` = the same
+metric with the inputs copied from pinned host memory and the lists, counts
+and densities copied back inside the timed region.  With --impl reference the
+CPU oracle is timed instead (a bounded sample, on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "neighbor pairs/s (build+find) at 1e7 particles; batched vs plain; p99 latency ms"
+UNIT = "pairs/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ---------------------------------------------------------------- workload
+def make_workload(name: str):
+    from paper_1910_02639_gb300 import workloads as wl
+    if name == "slab1e7":
+        s = wl.jittered_slab(400, 250, 100, jitter=0.1, h=1.5, seed=1913)
+        cfg = dict(workload="jittered_slab_1e7", n=s.n, lattice=[400, 250, 100], jitter=0.1,
+                   h=1.5, masses="1/N", bucket_size=16, alpha=0.5, beta=0.5, ngmax=256)
+    elif name == "slab2e6":
+        s = wl.jittered_slab(200, 100, 100, jitter=0.1, h=1.5, seed=1916)
+        cfg = dict(workload="jittered_slab_2e6", n=s.n, lattice=[200, 100, 100], jitter=0.1,
+                   h=1.5, masses="1/N", bucket_size=16, alpha=0.5, beta=0.5, ngmax=256)
+    elif name == "uniform32k":
+        s = wl.uniform_cube(32768, seed=1911)
+        cfg = dict(workload="uniform_cube_32768", n=s.n, target_neighbours=100,
+                   bucket_size=16, alpha=0.5, beta=0.5, ngmax=256)
+    elif name == "evrard1e6":
+        s = wl.evrard(1_000_000, seed=1912)
+        cfg = dict(workload="evrard_1e6", n=s.n, target_neighbours=100, bucket_size=16,
+                   alpha=0.5, beta=0.5, ngmax=512)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return s, cfg
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def find_kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("bt_find.cu", "bt_sort.cuh", "bt_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1910_02639_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the find kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", f"k_find_{workload}.md")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_sha") != find_kernel_sha():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_scaled"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [l for (t, l) in self.lines if t0 <= t <= t1] or [l for (_, l) in self.lines]
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- dist
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        return dist, dist.get_rank(), ws
+    return None, 0, 1
+
+
+def barrier(dist, dev):
+    import torch
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier(device_ids=[dev.index])
+
+
+def reduce_max(dist, v, dev):
+    if not dist:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_1910_02639_gb300 as bt
+
+    dist, rank, ws = dist_init()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    s, cfg = make_workload(args.workload)
+    n, ngmax, sb = s.n, cfg["ngmax"], cfg["bucket_size"]
+    cfg.update(parallelism="replicas" if ws > 1 else "single",
+               l2="no flush: positions (16 B x n) and lists (4 B x ngmax x n) exceed the 129 MB L2",
+               density="M4 cubic spline fused into the find pass")
+    stream = torch.cuda.current_stream(dev)
+    x, y, z, h, m = (torch.from_numpy(a).to(dev) for a in (s.x, s.y, s.z, s.h, s.m))
+    nb = torch.empty(n * ngmax, dtype=torch.int32, device=dev)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev)
+    rho = torch.empty(n, dtype=torch.float32, device=dev)
+    tree = None
+
+    def step():
+        nonlocal tree
+        tree = bt.btree_build(x, y, z, h, bucket_size=sb, alpha=cfg["alpha"], beta=cfg["beta"],
+                              stream=stream, tree=tree)
+        bt.btree_find_neighbors_density(tree, m, ngmax, nb, cnt, rho, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    barrier(dist, dev)
+    pairs = int(cnt.to(torch.int64).sum().item())
+    written = int(torch.clamp(cnt, max=ngmax).to(torch.int64).sum().item())
+
+    # ---- timed region: inputs resident in HBM
+    K = args.steps
+    f0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    f1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    l0 = bt.btree_kernel_launches()
+    barrier(dist, dev)
+    t0 = time.time()
+    e0.record(stream)
+    build_ms = []
+    for k in range(K):
+        tree = bt.btree_build(x, y, z, h, bucket_size=sb, alpha=cfg["alpha"], beta=cfg["beta"],
+                              stream=stream, tree=tree)
+        build_ms.append(bt.btree_get_info(tree)["build_ms"])
+        f0[k].record(stream)
+        bt.btree_find_neighbors_density(tree, m, ngmax, nb, cnt, rho, stream=stream)
+        f1[k].record(stream)
+    e1.record(stream)
+    barrier(dist, dev)
+    t1 = time.time()
+    launches = bt.btree_kernel_launches() - l0
+    time.sleep(0.2)
+    sampler.stop()
+    step_ms = e0.elapsed_time(e1) / K
+    find_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(f0, f1))
+    step_ms_max = reduce_max(dist, step_ms, dev)
+    value = pairs * ws / (step_ms_max * 1e-3)
+
+    peak, peak_kind = measured_hbm_peak()
+    alg_bytes = n * (16 + 4 + 4 + 4) + 4 * written  # x,y,z,h + m read; count, rho, rows written
+    achieved = alg_bytes / (find_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(cfg["workload"])
+    roofline = {"bound": "hbm", "kernel": "k_find<density> (+k_mass_to_tree)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind}
+    step_ach = alg_bytes / (step_ms * 1e-3) / 1e9
+    step_roofline = {"achieved": round(step_ach, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(step_ach / peak, 4), "note": "same algorithmic bytes over build+find"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+           "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": cfg, "impl": "gb300",
+           "pairs_per_step": pairs, "particles_per_s": n * ws / (step_ms_max * 1e-3),
+           "build_ms": round(statistics.mean(build_ms), 4), "find_ms": round(find_ms, 4),
+           "roofline": roofline, "step_roofline": step_roofline,
+           "gpu_launches": int(launches),
+           "clocks": sampler.summary(t0, t1)}
+
+    # ---- end to end through the public API, host buffers
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(args, bt, s, cfg, dev, stream, dist, ws, pairs)
+
+    # ---- CPU oracle on the host cores (rank 0, N = 1)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(s, cfg, args.cpu_sample)
+
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, bt, s, cfg, dev, stream, dist, ws, pairs):
+    import torch
+    n, ngmax = s.n, cfg["ngmax"]
+    hx = [torch.from_numpy(a).pin_memory() for a in (s.x, s.y, s.z, s.h, s.m)]
+    dx = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(5)]
+    nb = torch.empty(n * ngmax, dtype=torch.int32, device=dev)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev)
+    rho = torch.empty(n, dtype=torch.float32, device=dev)
+    h_nb = torch.empty(n * ngmax, dtype=torch.int32).pin_memory()
+    h_cnt = torch.empty(n, dtype=torch.int32).pin_memory()
+    h_rho = torch.empty(n, dtype=torch.float32).pin_memory()
+    tree = None
+
+    def step():
+        nonlocal tree
+        for d, hsrc in zip(dx, hx):
+            d.copy_(hsrc, non_blocking=True)
+        tree = bt.btree_build(dx[0], dx[1], dx[2], dx[3], bucket_size=cfg["bucket_size"],
+                              alpha=cfg["alpha"], beta=cfg["beta"], stream=stream, tree=tree)
+        bt.btree_find_neighbors_density(tree, dx[4], ngmax, nb, cnt, rho, stream=stream)
+        h_nb.copy_(nb, non_blocking=True)
+        h_cnt.copy_(cnt, non_blocking=True)
+        h_rho.copy_(rho, non_blocking=True)
+
+    for _ in range(2):
+        step()
+    K = max(1, min(args.steps, args.e2e_steps))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(dist, dev)
+    e0.record(stream)
+    for _ in range(K):
+        step()
+    e1.record(stream)
+    barrier(dist, dev)
+    ms = reduce_max(dist, e0.elapsed_time(e1) / K, dev)
+    del h_nb
+    return {"value": pairs * ws / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": K,
+            "h2d_bytes_per_step": 5 * 4 * n, "d2h_bytes_per_step": 4 * n * ngmax + 8 * n}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_baseline(s, cfg, sample):
+    """The oracle as it stands: BuildTree over the whole set, FindNeighbors for
+    a contiguous sample of queries; the build time is charged pro rata."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    n = s.n
+    q = min(sample, n)
+    q0 = (n - q) // 2
+    t0 = time.perf_counter()
+    tr = oracle.OracleTree(s.x, s.y, s.z, bucket_size=cfg["bucket_size"], alpha=cfg["alpha"],
+                           beta=cfg["beta"])
+    t1 = time.perf_counter()
+    _, c = tr.find(s.h, cfg["ngmax"], q0, q0 + q)
+    t2 = time.perf_counter()
+    pairs = int(np.asarray(c, dtype=np.int64).sum())
+    secs = (t1 - t0) * q / n + (t2 - t1)
+    return {"value": pairs / secs, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"BuildTree on all {n} particles ({t1 - t0:.2f} s, charged pro rata) + "
+                      f"FindNeighbors for particles [{q0}, {q0 + q}) ({t2 - t1:.2f} s), {pairs} pairs",
+            "build_s": round(t1 - t0, 3), "find_s": round(t2 - t1, 3)}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle on the host cores, on the same
+    workload and metric; each step a bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    oracle.build()
+    s, cfg = make_workload(args.workload)
+    n = s.n
+    q = min(args.ref_sample, n)
+    times, pairs_l = [], []
+    for k in range(args.warmup + args.steps):
+        q0 = (k * q) % max(n - q, 1)
+        t0 = time.perf_counter()
+        tr = oracle.OracleTree(s.x, s.y, s.z, bucket_size=cfg["bucket_size"], alpha=cfg["alpha"],
+                               beta=cfg["beta"])
+        t1 = time.perf_counter()
+        _, c = tr.find(s.h, cfg["ngmax"], q0, q0 + q)
+        t2 = time.perf_counter()
+        del tr
+        if k >= args.warmup:
+            times.append((t1 - t0) * q / n + (t2 - t1))
+            pairs_l.append(int(np.asarray(c, dtype=np.int64).sum()))
+    value = sum(pairs_l) / sum(times)
+    cores = oracle.num_threads()
+    sample = (f"per step: oracle BuildTree on all {n} particles (charged pro rata {q}/{n}) + "
+              f"FindNeighbors for {q} consecutive particles")
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": cfg, "impl": "reference",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="slab1e7")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1_000_000)
+    ap.add_argument("--ref-sample", type=int, default=200_000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

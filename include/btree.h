@@ -194,6 +194,11 @@ const char *btree_strerror(int status);
 /* Library version string. */
 const char *btree_version(void);
 
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all trees).  For instrumentation: the difference across a region
+ * is the number of kernel launches the region made. */
+uint64_t btree_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,8 @@ import threading
 __all__ = [
     "BtreeError", "Tree", "btree_build", "btree_find_neighbors",
     "btree_find_neighbors_density", "sph_density", "btree_status", "btree_get_info",
-    "btree_export", "btree_free", "btree_strerror", "btree_version", "library_path",
+    "btree_export", "btree_free", "btree_strerror", "btree_version", "btree_kernel_launches",
+    "library_path",
     "BT_OK", "BT_WARN_NGMAX", "BT_WARN_OVERSIZED_LEAF",
 ]
 
@@ -89,6 +90,8 @@ def _load():
         lib.btree_strerror.argtypes = [ctypes.c_int]
         lib.btree_version.restype = ctypes.c_char_p
         lib.btree_version.argtypes = []
+        lib.btree_kernel_launches.restype = ctypes.c_uint64
+        lib.btree_kernel_launches.argtypes = []
         _lib = lib
         return lib
 
@@ -242,3 +245,8 @@ def btree_strerror(status: int) -> str:
 
 def btree_version() -> str:
     return _load().btree_version().decode()
+
+
+def btree_kernel_launches() -> int:
+    """CUDA kernels launched by the library so far in this process."""
+    return int(_load().btree_kernel_launches())

@@ -4,6 +4,7 @@
 #include "bt_find.cuh"
 #include "bt_internal.cuh"
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -11,6 +12,11 @@
 #include <new>
 
 using namespace bt;
+
+namespace bt {
+static std::atomic<uint64_t> g_launches{0};
+void note_launch(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+}  // namespace bt
 
 struct btree {
     int64_t n = 0;
@@ -42,6 +48,8 @@ struct btree {
     Counters *ctr = nullptr;
     Counters *hctr = nullptr;  // pinned host mirror
     float *smass = nullptr;
+    int *halve_thr = nullptr;   // device [kMaxB+1]
+    int *hhalve_thr = nullptr;  // pinned host copy
 
     int ngroups = 0;
     bt_info info{};
@@ -98,6 +106,8 @@ void free_all(btree *t)
     for (int k = 0; k < 2; k++) { dev_free(t, t->wpos[k]); dev_free(t, t->wh[k]); dev_free(t, t->big_ids[k]); }
     dev_free(t, t->hist); dev_free(t, t->hoff); dev_free(t, t->cursor); dev_free(t, t->tiles);
     dev_free(t, t->big); dev_free(t, t->small); dev_free(t, t->ctr); dev_free(t, t->smass);
+    dev_free(t, t->halve_thr);
+    t->halve_thr = nullptr;
     t->geom = nullptr; t->walk = nullptr; t->slots = nullptr; t->groups = nullptr;
     t->spos = nullptr; t->sh = nullptr; t->inv = nullptr;
     for (int k = 0; k < 2; k++) { t->wpos[k] = nullptr; t->wh[k] = nullptr; t->big_ids[k] = nullptr; }
@@ -120,6 +130,7 @@ TreeDev view(const btree *t)
     T.sh = t->sh;
     T.inv = t->inv;
     T.ctr = t->ctr;
+    T.halve_thr = t->halve_thr;
     T.cap_nodes = t->cap_nodes;
     T.cap_slots = t->cap_slots;
     T.cap_groups = t->cap_groups;
@@ -174,6 +185,10 @@ int ensure_particle_caps(btree *t, int64_t n)
         t->ctr = static_cast<Counters *>(dev_alloc(t, sizeof(Counters)));
         if (!t->ctr) return BT_ERR_OOM;
     }
+    if (!t->halve_thr) {
+        t->halve_thr = static_cast<int *>(dev_alloc(t, sizeof(int) * (kMaxB + 1)));
+        if (!t->halve_thr) return BT_ERR_OOM;
+    }
     return BT_OK;
 }
 
@@ -204,6 +219,14 @@ int do_build(btree *t, const float *x, const float *y, const float *z, const flo
     const int n = (int)t->n;
     cudaStream_t st = t->st;
     TreeDev T = view(t);
+    // Eq. 4 acceptance bound per b for this beta: halve iff u > beta*b^3 in
+    // binary64, i.e. iff u > floor(beta*b^3) (u is an integer).
+    for (int b = 0; b <= kMaxB; b++) {
+        const double bb = (double)b * (double)b * (double)b;
+        const double thr = t->beta * bb;
+        t->hhalve_thr[b] = thr < 0.0 ? -1 : (thr >= 2147483647.0 ? INT32_MAX : (int)std::floor(thr));
+    }
+    cudaMemcpyAsync(t->halve_thr, t->hhalve_thr, sizeof(int) * (kMaxB + 1), cudaMemcpyHostToDevice, st);
     launch_init_counters(t->ctr, st);
     cudaEventRecord(t->ev0, st);
     launch_bbox(x, y, z, h, n, t->ctr, t->sms, st);
@@ -239,11 +262,12 @@ int do_build(btree *t, const float *x, const float *y, const float *z, const flo
             for (int it = 0; it < 16; it++) {
                 launch_set_int(&t->ctr->again, 0, st);
                 launch_big_hist(T, t->big, nb, chunks, src, t->hist, t->sms, st);
-                launch_big_ratio(t->big, nb, t->hist, na, t->beta, t->ctr, st);
+                launch_big_ratio(t->big, nb, t->hist, hist_total, na, t->halve_thr, t->ctr, t->sms, st);
                 if ((rc = read_counters(t)) != BT_OK) return rc;
                 if (!t->hctr->again) break;
+                launch_big_zero(t->big, nb, t->hist, hist_total, t->sms, st);
             }
-            launch_big_finish(T, t->big, nb, t->hist, (int)nslots, st);
+            launch_big_finish(T, t->big, nb, (int)nslots, st);
             nslots += hist_total;
             launch_set_int(&t->ctr->nslots, (int)nslots, st);
             launch_scan(t->hist, hist_total, t->tiles, t->hoff, st);
@@ -319,6 +343,7 @@ int btree_build(const float *x, const float *y, const float *z, const float *h, 
         cudaGetDevice(&t->device);
         cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, t->device);
         if (cudaMallocHost(&t->hctr, sizeof(Counters)) != cudaSuccess ||
+            cudaMallocHost(&t->hhalve_thr, sizeof(int) * (kMaxB + 1)) != cudaSuccess ||
             cudaEventCreate(&t->ev0) != cudaSuccess || cudaEventCreate(&t->ev1) != cudaSuccess) {
             cudaGetLastError();
             delete t;
@@ -495,6 +520,7 @@ void btree_free(btree_t *t)
     if (!t) return;
     free_all(t);
     if (t->hctr) cudaFreeHost(t->hctr);
+    if (t->hhalve_thr) cudaFreeHost(t->hhalve_thr);
     if (t->ev0) cudaEventDestroy(t->ev0);
     if (t->ev1) cudaEventDestroy(t->ev1);
     delete t;
@@ -517,5 +543,7 @@ const char *btree_strerror(int status)
 }
 
 const char *btree_version(void) { return "btree-gb300 0.1 (sm_103a)"; }
+
+uint64_t btree_kernel_launches(void) { return bt::g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

@@ -112,7 +112,12 @@ __global__ void k_big_setup(TreeDev T, BigCell *big, const int *ids, int nb)
     c.chunk_base = (g.count + kBigChunk - 1) / kBigChunk;
     c.state = 0;
     c.slot0 = 0;
+    c.u = 0;
+    c.ne = 0;
+    c.lastj = -1;
+    c.halved = 0;
     c.pad = 0;
+    c.w[0] = c.w[1] = c.w[2] = 0.0;
     big[i] = c;
 }
 
@@ -224,71 +229,97 @@ __global__ void __launch_bounds__(256) k_big_hist(TreeDev T, const BigCell *big,
     }
 }
 
-// Ratio test (Eq. 4), one block per big cell.
-__global__ void __launch_bounds__(256) k_big_ratio(BigCell *big, int *hist, int na, double beta,
-                                                   Counters *ctr)
+// Per-cell statistics of the current histogram (Eq. 4 numerator, non-empty
+// sub-cells), accumulated over the whole level by all blocks.
+__global__ void __launch_bounds__(256) k_big_count(BigCell *big, int nb, const int *hist, int total,
+                                                   int na)
 {
-    BigCell &c = big[blockIdx.x];
-    if (c.state != 0) return;
-    const int b = c.b;
-    const int ncell = b * b * b;
-    const int *hc = hist + c.hist_base;
-    int u = 0;
-    for (int j = threadIdx.x; j < ncell; j += blockDim.x) u += hc[j] <= na;
-    __shared__ int s_u[8];
-    __shared__ int s_halve;
-    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(~0u, u, o);
-    if ((threadIdx.x & 31) == 0) s_u[threadIdx.x >> 5] = u;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int tot = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); k++) tot += s_u[k];
-        bool halve = ((double)tot > __dmul_rn(beta, (double)ncell)) && b > 2;
-        s_halve = halve;
-        if (halve) {
-            c.b = max(2, b / 2);
-            ctr->again = 1;
-        } else {
-            c.state = 1;
+    for (int e0 = blockIdx.x * blockDim.x; e0 < total; e0 += gridDim.x * blockDim.x) {
+        const int e = e0 + threadIdx.x;
+        int ci = -1, u = 0, ne = 0, lj = -1;
+        if (e < total) {
+            ci = find_cell_by_hist(big, nb, e);
+            const BigCell &c = big[ci];
+            const int j = e - c.hist_base;
+            if (c.state == 0 && j < c.b * c.b * c.b) {
+                const int v = hist[e];
+                u = v <= na;
+                ne = v > 0;
+                lj = v > 0 ? j : -1;
+            } else {
+                ci = -1;
+            }
         }
-    }
-    __syncthreads();
-    if (s_halve) {
-        int *hw = hist + c.hist_base;
-        const int n0 = c.b0 * c.b0 * c.b0;
-        for (int j = threadIdx.x; j < n0; j += blockDim.x) hw[j] = 0;
+        // one atomic per warp when the whole warp lies in one cell (the
+        // common case: cells are long contiguous runs of e), else per lane
+        const unsigned same = __match_any_sync(~0u, ci);
+        if (same == 0xffffffffu) {
+            int su = u, sne = ne, slj = lj;
+            for (int o = 16; o > 0; o >>= 1) {
+                su += __shfl_xor_sync(~0u, su, o);
+                sne += __shfl_xor_sync(~0u, sne, o);
+                slj = max(slj, __shfl_xor_sync(~0u, slj, o));
+            }
+            if (ci >= 0 && (threadIdx.x & 31) == 0) {
+                if (su) atomicAdd(&big[ci].u, su);
+                if (sne) atomicAdd(&big[ci].ne, sne);
+                if (slj >= 0) atomicMax(&big[ci].lastj, slj);
+            }
+        } else if (ci >= 0) {
+            if (u) atomicAdd(&big[ci].u, u);
+            if (ne) atomicAdd(&big[ci].ne, ne);
+            if (lj >= 0) atomicMax(&big[ci].lastj, lj);
+        }
     }
 }
 
-// After acceptance: no-progress guard, walk parameters, slot placement.
-__global__ void __launch_bounds__(256) k_big_finish(TreeDev T, BigCell *big, const int *hist,
-                                                    int slot_level_base)
+// Ratio test (Eq. 4), one thread per big cell: accept b or halve it.
+__global__ void k_big_decide(BigCell *big, int nb, const int *halve_thr, Counters *ctr)
 {
-    BigCell &c = big[blockIdx.x];
-    const int b = c.b;
-    const int ncell = b * b * b;
-    const int *hc = hist + c.hist_base;
-    int nonempty = 0, last = -1;
-    for (int j = threadIdx.x; j < ncell; j += blockDim.x)
-        if (hc[j] > 0) { nonempty++; last = j; }
-    __shared__ int s_ne[8], s_last[8];
-    for (int o = 16; o > 0; o >>= 1) {
-        nonempty += __shfl_xor_sync(~0u, nonempty, o);
-        last = max(last, __shfl_xor_sync(~0u, last, o));
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    BigCell &c = big[i];
+    c.halved = 0;
+    if (c.state != 0) return;
+    if (c.u > halve_thr[c.b] && c.b > 2) {
+        c.b = max(2, c.b / 2);
+        c.halved = 1;
+        c.u = 0;
+        c.ne = 0;
+        c.lastj = -1;
+        ctr->again = 1;
+    } else {
+        c.state = 1;
     }
-    if ((threadIdx.x & 31) == 0) { s_ne[threadIdx.x >> 5] = nonempty; s_last[threadIdx.x >> 5] = last; }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    int ne = 0, lj = -1;
-    for (int k = 0; k < (int)(blockDim.x >> 5); k++) { ne += s_ne[k]; lj = max(lj, s_last[k]); }
+}
+
+// Clear the histogram of every cell whose b was just halved.
+__global__ void __launch_bounds__(256) k_big_zero(const BigCell *big, int nb, int *hist, int total)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const BigCell &c = big[find_cell_by_hist(big, nb, e)];
+        if (c.halved) hist[e] = 0;
+    }
+}
+
+// After acceptance, one thread per cell: no-progress guard, walk
+// parameters, sub-cell widths, slot placement.
+__global__ void k_big_finish(TreeDev T, BigCell *big, int nb, int slot_level_base)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    BigCell &c = big[i];
+    const int b = c.b;
     const NodeGeom g = T.geom[c.node];
+    for (int l = 0; l < 3; l++) c.w[l] = cell_width(g.lo[l], g.hi[l], b);
     bool leaf = false;
-    if (ne == 1) {
+    if (c.ne == 1) {
+        const int lj = c.lastj;
         int cc[3] = {lj % b, (lj / b) % b, lj / (b * b)};
         bool same = true;
         for (int l = 0; l < 3; l++) {
             double clo, chi;
-            child_bounds(g.lo[l], g.hi[l], b, cc[l], clo, chi);
+            child_bounds_w(g.lo[l], g.hi[l], c.w[l], b, cc[l], clo, chi);
             if (clo != g.lo[l] || chi != g.hi[l]) same = false;
         }
         leaf = same;
@@ -344,7 +375,8 @@ __global__ void __launch_bounds__(256) k_big_emit(TreeDev T, const BigCell *big,
             } else {
                 NodeGeom cg;
                 int cc[3] = {j % b, (j / b) % b, j / (b * b)};
-                for (int l = 0; l < 3; l++) child_bounds(g.lo[l], g.hi[l], b, cc[l], cg.lo[l], cg.hi[l]);
+                for (int l = 0; l < 3; l++)
+                    child_bounds_w(g.lo[l], g.hi[l], c.w[l], b, cc[l], cg.lo[l], cg.hi[l]);
                 cg.start = start;
                 cg.count = cnt;
                 cg.depth = depth;
@@ -491,8 +523,11 @@ __global__ void __launch_bounds__(256) k_scan_apply(const int *in, int n, const 
 // ------------------------------------------------------------------ warp builder
 struct Frame {
     double lo[3], hi[3];
+    double w[3];  // sub-cell widths once split
     int a, m, node, depth;
-    int b, slot0, next, emit;
+    int b, slot0, next;
+    int emit;   // emit work units for the leaves below this cell
+    int eself;  // emit this cell itself as one or two work units
 };
 
 constexpr int kSmallWarps = 4;
@@ -552,8 +587,9 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
             Frame &f = S.fr[0];
             for (int l = 0; l < 3; l++) { f.lo[l] = G.lo[l]; f.hi[l] = G.hi[l]; }
             f.a = 0; f.m = m0; f.node = item.node; f.depth = G.depth;
-            f.b = 0; f.slot0 = 0; f.next = 0; f.emit = m0 > kGroupMax;
-            if (m0 <= kGroupMax) emit_groups(T, base, m0);
+            f.b = 0; f.slot0 = 0; f.next = 0;
+            f.emit = m0 > kWholeMax;
+            f.eself = m0 <= kWholeMax;
         }
         int sp = 1;
         __syncwarp();
@@ -582,7 +618,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                     int u = 0;
                     for (int j = lane; j < ncell; j += 32) u += S.hist[j] <= na;
                     u = warp_sum(u);
-                    if ((double)u > __dmul_rn(beta, (double)ncell) && b > 2) {
+                    if (u > T.halve_thr[b] && b > 2) {
                         b = max(2, b / 2);
                         __syncwarp();
                         continue;
@@ -590,6 +626,9 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                     break;
                 }
                 const int ncell = b * b * b;
+                if (lane == 0)
+                    for (int l = 0; l < 3; l++) F.w[l] = cell_width(g.lo[l], g.hi[l], b);
+                __syncwarp();
                 // no-progress guard
                 int ne = 0, lj = -1;
                 for (int j = lane; j < ncell; j += 32)
@@ -602,7 +641,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                     bool same = true;
                     for (int l = 0; l < 3; l++) {
                         double clo, chi;
-                        child_bounds(g.lo[l], g.hi[l], b, cc[l], clo, chi);
+                        child_bounds_w(g.lo[l], g.hi[l], F.w[l], b, cc[l], clo, chi);
                         if (clo != g.lo[l] || chi != g.hi[l]) same = false;
                     }
                     leaf = same;
@@ -615,7 +654,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                         T.walk[F.node] = w;
                         atomicAdd(&T.ctr->noversized, 1);
                         atomicOr(&T.ctr->status, kStOversized);
-                        if (F.emit) emit_groups(T, base + a, m);
+                        if (F.emit || F.eself) emit_groups(T, base + a, m);
                     }
                     sp--;
                     __syncwarp();
@@ -634,6 +673,28 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                         }
                         if (j < ncell) S.off[j] = carry + incl - v;
                         carry += __shfl_sync(~0u, incl, 31);
+                    }
+                }
+                __syncwarp();
+                // a cell of <= kWholeMax particles becomes two work units, split
+                // at the sub-cell boundary nearest its middle (contiguous, and
+                // compact: sub-cell ids run x fastest, so low ids are low z)
+                if (F.eself && lane == 0) {
+                    if (m <= kGroupMax) {
+                        emit_groups(T, base + a, m);
+                    } else {
+                        int bnd = 0, best = m;
+                        for (int j = 0; j <= ncell; j++) {
+                            const int o = j < ncell ? S.off[j] : m;
+                            const int d = abs(2 * o - m);
+                            if (d < best) { best = d; bnd = o; }
+                        }
+                        if (bnd == 0 || bnd == m) {
+                            emit_groups(T, base + a, m);
+                        } else {
+                            emit_groups(T, base + a, bnd);
+                            emit_groups(T, base + a + bnd, m - bnd);
+                        }
                     }
                 }
                 int slot0 = 0;
@@ -664,10 +725,9 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                             NodeGeom cg;
                             int cc[3] = {j % b, (j / b) % b, j / (b * b)};
                             for (int l = 0; l < 3; l++)
-                                child_bounds(g.lo[l], g.hi[l], b, cc[l], cg.lo[l], cg.hi[l]);
+                                child_bounds_w(g.lo[l], g.hi[l], F.w[l], b, cc[l], cg.lo[l], cg.hi[l]);
                             cg.start = start; cg.count = cnt; cg.depth = depth; cg.pad = 0;
                             T.geom[child] = cg;
-                            if (F.emit && cnt <= kGroupMax) emit_groups(T, start, cnt);
                         }
                     } else if (cnt > 0) {
                         if (cnt > T.s) {
@@ -724,9 +784,12 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                     Frame &C = S.fr[sp];
                     const int b = F.b;
                     int cc[3] = {found % b, (found / b) % b, found / (b * b)};
-                    for (int l = 0; l < 3; l++) child_bounds(F.lo[l], F.hi[l], b, cc[l], C.lo[l], C.hi[l]);
+                    for (int l = 0; l < 3; l++)
+                        child_bounds_w(F.lo[l], F.hi[l], F.w[l], b, cc[l], C.lo[l], C.hi[l]);
                     C.a = s.start - base; C.m = s.count; C.node = s.child; C.depth = F.depth + 1;
-                    C.b = 0; C.slot0 = 0; C.next = 0; C.emit = F.emit && s.count > kGroupMax;
+                    C.b = 0; C.slot0 = 0; C.next = 0;
+                    C.emit = F.emit && s.count > kWholeMax;
+                    C.eself = F.emit && s.count <= kWholeMax;
                 }
                 sp++;
                 __syncwarp();
@@ -757,47 +820,68 @@ static inline int grid_for(long long work, int per_block, int max_blocks)
 void launch_bbox(const float *x, const float *y, const float *z, const float *h, int n,
                  Counters *ctr, int sms, cudaStream_t st)
 {
+    note_launch();
     k_bbox<<<grid_for(n, 256 * 8, sms * 8), 256, 0, st>>>(x, y, z, h, n, ctr);
 }
 
-void launch_root(const TreeDev &T, int n, cudaStream_t st) { k_root<<<1, 1, 0, st>>>(T, n); }
+void launch_root(const TreeDev &T, int n, cudaStream_t st)
+{
+    note_launch();
+    k_root<<<1, 1, 0, st>>>(T, n);
+}
 
 void launch_root_leaf(const TreeDev &T, const float *x, const float *y, const float *z,
                       const float *h, int n, int sms, cudaStream_t st)
 {
+    note_launch();
     k_root_leaf<<<grid_for(n, 256, sms * 4), 256, 0, st>>>(T, x, y, z, h, n);
 }
 
 void launch_big_setup(const TreeDev &T, BigCell *big, const int *ids, int nb, cudaStream_t st)
 {
+    note_launch();
     k_big_setup<<<grid_for(nb, 256, 1 << 20), 256, 0, st>>>(T, big, ids, nb);
+    note_launch();
     k_big_scan<<<1, 1024, 0, st>>>(big, nb, T.ctr);
 }
 
 void launch_big_hist(const TreeDev &T, const BigCell *big, int nb, int chunks, Src src, int *hist,
                      int sms, cudaStream_t st)
 {
+    note_launch();
     k_big_hist<<<grid_for(chunks, 1, sms * 8), 256, 0, st>>>(T, big, nb, src, hist);
 }
 
-void launch_big_ratio(BigCell *big, int nb, int *hist, int na, double beta, Counters *ctr,
-                      cudaStream_t st)
+void launch_big_ratio(BigCell *big, int nb, const int *hist, int hist_total, int na,
+                      const int *halve_thr, Counters *ctr, int sms, cudaStream_t st)
 {
-    k_big_ratio<<<nb, 256, 0, st>>>(big, hist, na, beta, ctr);
+    note_launch();
+    k_big_count<<<grid_for(hist_total, 256, sms * 8), 256, 0, st>>>(big, nb, hist, hist_total, na);
+    note_launch();
+    k_big_decide<<<grid_for(nb, 128, 1 << 20), 128, 0, st>>>(big, nb, halve_thr, ctr);
 }
 
-void launch_big_finish(const TreeDev &T, BigCell *big, int nb, const int *hist, int slot_level_base,
-                       cudaStream_t st)
+void launch_big_zero(const BigCell *big, int nb, int *hist, int hist_total, int sms, cudaStream_t st)
 {
-    k_big_finish<<<nb, 256, 0, st>>>(T, big, hist, slot_level_base);
+    note_launch();
+    k_big_zero<<<grid_for(hist_total, 256, sms * 8), 256, 0, st>>>(big, nb, hist, hist_total);
+}
+
+void launch_big_finish(const TreeDev &T, BigCell *big, int nb, int slot_level_base, cudaStream_t st)
+{
+    note_launch();
+    k_big_finish<<<grid_for(nb, 128, 1 << 20), 128, 0, st>>>(T, big, nb, slot_level_base);
 }
 
 void launch_scan(const int *in, int n, int *tile_buf, int *out, cudaStream_t st)
 {
     int ntiles = (n + kScanTile - 1) / kScanTile;
     if (ntiles < 1) ntiles = 1;
+    note_launch();
     k_scan_tiles<<<ntiles, 256, 0, st>>>(in, n, tile_buf);
+    note_launch();
     k_scan_tile_sums<<<1, 1024, 0, st>>>(tile_buf, ntiles);
+    note_launch();
     k_scan_apply<<<ntiles, 256, 0, st>>>(in, n, tile_buf, out);
 }
 
@@ -807,6 +891,7 @@ void launch_big_emit(const TreeDev &T, const BigCell *big, int nb, int hist_tota
                      const int *hoff, int *cursor, int dst_buf, int *next_big, SmallItem *small,
                      int sms, cudaStream_t st)
 {
+    note_launch();
     k_big_emit<<<grid_for(hist_total, 256, sms * 16), 256, 0, st>>>(T, big, nb, hist, hoff, cursor,
                                                                      dst_buf, next_big, small);
 }
@@ -814,6 +899,7 @@ void launch_big_emit(const TreeDev &T, const BigCell *big, int nb, int hist_tota
 void launch_big_scatter(const TreeDev &T, const BigCell *big, int nb, int chunks, Src src,
                         int *cursor, float4 *dst_pos, float *dst_h, int sms, cudaStream_t st)
 {
+    note_launch();
     k_big_scatter<<<grid_for(chunks, 1, sms * 8), 256, 0, st>>>(T, big, nb, src, cursor, dst_pos,
                                                                 dst_h);
 }
@@ -823,6 +909,7 @@ void launch_small(const TreeDev &T, const SmallItem *items, int nitems, Src src0
 {
     if (nitems <= 0) return;
     int blocks = grid_for(nitems, kSmallWarps, sms * 4);
+    note_launch();
     k_small<<<blocks, 32 * kSmallWarps, small_smem_bytes(), st>>>(T, items, nitems, src0, src1,
                                                                    srcin, na, beta);
 }
@@ -857,11 +944,20 @@ __global__ void k_set_small_root(SmallItem *small, int *big_ids, int n, int s, C
     }
 }
 
-void launch_init_counters(Counters *ctr, cudaStream_t st) { k_init_counters<<<1, 1, 0, st>>>(ctr); }
-void launch_set_int(int *p, int v, cudaStream_t st) { k_set_int<<<1, 1, 0, st>>>(p, v); }
+void launch_init_counters(Counters *ctr, cudaStream_t st)
+{
+    note_launch();
+    k_init_counters<<<1, 1, 0, st>>>(ctr);
+}
+void launch_set_int(int *p, int v, cudaStream_t st)
+{
+    note_launch();
+    k_set_int<<<1, 1, 0, st>>>(p, v);
+}
 void launch_set_small_root(SmallItem *small, int *big_ids, int n, int s, Counters *ctr,
                            cudaStream_t st)
 {
+    note_launch();
     k_set_small_root<<<1, 1, 0, st>>>(small, big_ids, n, s, ctr);
 }
 

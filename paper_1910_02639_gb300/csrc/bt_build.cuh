@@ -12,10 +12,10 @@ void launch_root_leaf(const TreeDev &T, const float *x, const float *y, const fl
 void launch_big_setup(const TreeDev &T, BigCell *big, const int *ids, int nb, cudaStream_t st);
 void launch_big_hist(const TreeDev &T, const BigCell *big, int nb, int chunks, Src src, int *hist,
                      int sms, cudaStream_t st);
-void launch_big_ratio(BigCell *big, int nb, int *hist, int na, double beta, Counters *ctr,
-                      cudaStream_t st);
-void launch_big_finish(const TreeDev &T, BigCell *big, int nb, const int *hist, int slot_level_base,
-                       cudaStream_t st);
+void launch_big_ratio(BigCell *big, int nb, const int *hist, int hist_total, int na,
+                      const int *halve_thr, Counters *ctr, int sms, cudaStream_t st);
+void launch_big_zero(const BigCell *big, int nb, int *hist, int hist_total, int sms, cudaStream_t st);
+void launch_big_finish(const TreeDev &T, BigCell *big, int nb, int slot_level_base, cudaStream_t st);
 void launch_scan(const int *in, int n, int *tile_buf, int *out, cudaStream_t st);
 int scan_tile_count(int n);
 void launch_big_emit(const TreeDev &T, const BigCell *big, int nb, int hist_total, const int *hist,

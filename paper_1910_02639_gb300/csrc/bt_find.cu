@@ -1,23 +1,29 @@
 // bt_find.cu -- FindNeighbors (Algorithm 2 of arXiv:1910.02639) on the GPU,
 // optionally fused with the SPH density sum (M4 cubic spline).
 //
-// Work unit: a group of <= 32 particles that are contiguous in tree order (a
-// leaf, a small cell, or a 32-slice of an oversized leaf), one 128-thread
-// block at a time.  Per group:
-//   1. warp 0 loads the queries and walks the tree once for the union of
-//      their search intervals (Eqs. 5-6 on the group's query box), collecting
-//      contiguous particle ranges (whole x-runs of sub-cells, Eq. 3 order);
-//   2. all warps stream the candidates of those ranges (coalesced float4
-//      loads) and keep those within 2*h_max of the group's bounding box;
+// Work unit: a group of <= 32 particles contiguous in tree order (a leaf, a
+// cell of <= 32 particles, or a slice of an oversized leaf), one 256-thread
+// block at a time (blocks are persistent and stride over the groups).  Per
+// group:
+//   1. warp 0 loads the queries; then all threads walk the tree once for the
+//      union of their search intervals (Eqs. 5-6 applied to the group's query
+//      box), frontier by frontier, collecting contiguous particle ranges
+//      (x-runs of sub-cells in Eq. 3 order; internal sub-cells of <= 32
+//      particles are taken whole) as 32-particle jobs;
+//   2. all warps stream the jobs with several coalesced float4 loads in
+//      flight per lane and keep the candidates within 2*h_max of the group's
+//      bounding box;
 //   3. the kept candidates are sorted by original index (bitonic, registers);
-//   4. each candidate chunk of 32 is tested against every query with an FP32
-//      filter whose error band is certified; the rare pairs inside the band
+//   4. stage A: every 32-candidate chunk is tested against every query with
+//      an FP32 filter whose error band is certified; pairs inside the band
 //      are decided by the binary64 definition; one ballot per (query, chunk);
-//   5. per query, the ballots are turned into the ascending, capped row with
-//      a warp prefix sum (and the density sum is accumulated in that order).
-// Groups whose candidate set is larger than the buffer, or spans too many
-// original indices for 32-bit sort keys, are processed in windows of
-// original index (same results, more passes).
+//   5. stage B: per query, the ballots are compacted (prefix sums) into a
+//      list of hit positions which the warp writes out lane-parallel as the
+//      ascending, capped row, accumulating the density terms in that order
+//      when fused.
+// Groups whose candidate set exceeds the buffer, or spans too many original
+// indices for 32-bit sort keys, are processed in windows of original index
+// (same results, more passes).
 #include "bt_internal.cuh"
 #include "bt_sort.cuh"
 #include "bt_find.cuh"
@@ -26,35 +32,45 @@
 
 namespace bt {
 
+constexpr int kFindThreads = 256;
+constexpr int kFindWarps = kFindThreads / 32;
 constexpr int kCap = 1024;                 // candidates per window
 constexpr int kSlotBits = 10;              // log2(kCap)
 constexpr int kSpanMax = (1 << 22) - 1;    // original-index span of one window
 constexpr int kChunks = kCap / 32;
-constexpr int kRangeMax = 256;
-constexpr int kStackMax = 128;
+constexpr int kJobMax = 512;               // 32-particle jobs per group walk
+constexpr int kFrontMax = 64;              // tree nodes per walk frontier
 constexpr int kDescendMin = 32;            // smaller internal sub-cells are scanned whole
 constexpr int kFindChunk = 4;              // consecutive groups per block step
+constexpr int kHitBatch = 256;             // hit positions staged per warp and pass
+constexpr int kUnroll = 4;                 // gather jobs in flight per warp
+constexpr int kSortThreads = 128;          // warps 0-3 sort; the others wait
 constexpr float kPiF = 3.14159265358979f;
 
 struct FindSmem {
-    float4 cand[kCap];
+    float4 cand[kCap];        // x, y, z, original index (bits)
     float cmass[kCap];
-    uint32_t key[kCap];
+    uint32_t key[kCap];       // (orig - kmin) << kSlotBits | slot, sorted
     uint32_t mask[kGroupMax * kChunks];
-    unsigned short rank_of[kCap];
+    // density partial sums: slot k of query p holds the terms whose position
+    // in p's ascending neighbour list is k mod 32, so the summation order
+    // depends on the list alone (not on windows or work-unit composition)
+    float qacc[kGroupMax][32];
+    unsigned short hits[kFindWarps][kHitBatch];
+    int2 jobs[kJobMax];       // (first tree position, length <= 32)
     float4 q[kGroupMax];      // x, y, z, R_lo
     float qrhi[kGroupMax];
     float qh[kGroupMax];
     int qorig[kGroupMax];
-    int qself[kGroupMax];
+    int qself[kGroupMax];     // sorted position of the query itself, or -1
     int qcnt[kGroupMax];
-    float qacc[kGroupMax];
-    int2 ranges[kRangeMax];
-    int stack[kStackMax];
+    int front[2][kFrontMax];  // walk frontiers
+    int fr_rx0[kFrontMax], fr_rx1[kFrontMax], fr_ry0[kFrontMax], fr_ny[kFrontMax];
+    int fr_rz0[kFrontMax], fr_row0[kFrontMax], fr_b[kFrontMax], fr_off[kFrontMax + 1];
     int hist[256];
     float box[13];            // PL[3] PH[3] QL[3] QH[3] T
-    int nrange, nstack, ncand, kmin, kmax, range_ovf, ovf_lo, ovf_hi;
-    int gstart, gcount, wlo, whi, mode_w;
+    int njobs, nfront, nnext, ncand, kmin, kmax, range_ovf, ovf_lo, ovf_hi;
+    int jfail, cover, gstart, gcount, whi;
 };
 
 struct FindArgs {
@@ -90,106 +106,159 @@ __device__ __forceinline__ bool exact_neighbor(float4 p, float hp, float4 qd)
     return d < __dmul_rn(two_h, two_h);
 }
 
+// Append a contiguous particle range as 32-particle jobs.
 __device__ __forceinline__ void add_range(FindSmem &S, int s, int len)
 {
     if (len <= 0) return;
-    int r = atomicAdd(&S.nrange, 1);
-    if (r < kRangeMax - 1) {
-        S.ranges[r] = make_int2(s, len);
+    const int nj = (len + 31) >> 5;
+    const int j0 = atomicAdd(&S.njobs, nj);
+    if (j0 + nj <= kJobMax) {
+        for (int k = 0; k < nj; k++) S.jobs[j0 + k] = make_int2(s + 32 * k, min(32, len - 32 * k));
     } else {
+        // jobs [0, jfail) were all written; everything else is covered by
+        // [ovf_lo, ovf_hi)
+        atomicMin(&S.jfail, j0);
         atomicMin(&S.ovf_lo, s);
         atomicMax(&S.ovf_hi, s + len);
         S.range_ovf = 1;
     }
 }
 
-// Warp 0: the tree walk for the group's query box.
-__device__ void group_walk(const TreeDev &T, FindSmem &S, int lane)
+// All threads: the tree walk for the group's query box, one frontier of
+// nodes at a time; the rows of all frontier nodes are spread over the block.
+__device__ void group_walk(const TreeDev &T, FindSmem &S)
 {
-    if (lane == 0) {
-        S.nrange = 0;
-        S.nstack = 0;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        S.njobs = 0;
+        S.cover = 0;
         S.range_ovf = 0;
+        S.jfail = kJobMax;
         S.ovf_lo = INT_MAX;
         S.ovf_hi = INT_MIN;
+        S.front[0][0] = 0;
+        S.nfront = 1;
+        S.nnext = 0;
     }
-    __syncwarp();
+    __syncthreads();
     const float QL0 = S.box[6], QL1 = S.box[7], QL2 = S.box[8];
     const float QH0 = S.box[9], QH1 = S.box[10], QH2 = S.box[11];
-    if (lane == 0) {
-        S.stack[0] = 0;
-        S.nstack = 1;
-    }
-    __syncwarp();
-    while (S.nstack > 0) {
-        const int nid = S.stack[S.nstack - 1];
-        __syncwarp();
-        if (lane == 0) S.nstack--;
-        const NodeWalk W = T.walk[nid];
-        __syncwarp();
-        if (W.b == 0) {
-            if (lane == 0) add_range(S, W.start, W.count);
-            __syncwarp();
-            continue;
+    int cur = 0;
+    for (;;) {
+        const int nf = S.nfront;
+        if (nf == 0) break;
+        // per-node ranges
+        if (tid < nf) {
+            const NodeWalk W = T.walk[S.front[cur][tid]];
+            int rows = 0;
+            if (W.b == 0) {
+                add_range(S, W.start, W.count);
+            } else {
+                int rx0, rx1, ry0, ry1, rz0, rz1;
+                walk_range(QL0, QH0, W, 0, rx0, rx1);
+                walk_range(QL1, QH1, W, 1, ry0, ry1);
+                walk_range(QL2, QH2, W, 2, rz0, rz1);
+                if (rx1 >= rx0 && ry1 >= ry0 && rz1 >= rz0) {
+                    rows = (ry1 - ry0 + 1) * (rz1 - rz0 + 1);
+                    S.fr_rx0[tid] = rx0;
+                    S.fr_rx1[tid] = rx1;
+                    S.fr_ry0[tid] = ry0;
+                    S.fr_ny[tid] = ry1 - ry0 + 1;
+                    S.fr_rz0[tid] = rz0;
+                    S.fr_row0[tid] = W.slot0;
+                    S.fr_b[tid] = W.b;
+                }
+            }
+            S.fr_off[tid] = rows;
         }
-        int rx0, rx1, ry0, ry1, rz0, rz1;
-        walk_range(QL0, QH0, W, 0, rx0, rx1);
-        walk_range(QL1, QH1, W, 1, ry0, ry1);
-        walk_range(QL2, QH2, W, 2, rz0, rz1);
-        if (rx1 < rx0 || ry1 < ry0 || rz1 < rz0) continue;
-        const int ny = ry1 - ry0 + 1;
-        const int nyz = ny * (rz1 - rz0 + 1);
-        for (int idx = lane; idx < nyz; idx += 32) {
-            const int cy = ry0 + idx % ny;
-            const int cz = rz0 + idx / ny;
-            const int row = W.slot0 + W.b * (cy + W.b * cz);
+        __syncthreads();
+        if (tid < 32) {  // exclusive prefix of rows over the frontier
+            int carry = 0;
+            for (int i0 = 0; i0 < nf; i0 += 32) {
+                const int i = i0 + tid;
+                const int v = i < nf ? S.fr_off[i] : 0;
+                int incl = v;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int t = __shfl_up_sync(~0u, incl, o);
+                    if (tid >= o) incl += t;
+                }
+                if (i < nf) S.fr_off[i] = carry + incl - v;
+                carry += __shfl_sync(~0u, incl, 31);
+            }
+            if (tid == 0) S.fr_off[nf] = carry;
+        }
+        __syncthreads();
+        const int total = S.fr_off[nf];
+        for (int r = tid; r < total; r += kFindThreads) {
+            int lo = 0, hi = nf - 1;  // frontier node owning row r
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (S.fr_off[mid] <= r) lo = mid; else hi = mid - 1;
+            }
+            const int lr = r - S.fr_off[lo];
+            const int ny = S.fr_ny[lo], b = S.fr_b[lo];
+            const int cy = S.fr_ry0[lo] + lr % ny;
+            const int cz = S.fr_rz0[lo] + lr / ny;
+            const int row = S.fr_row0[lo] + b * (cy + b * cz);
+            const int rx0 = S.fr_rx0[lo], rx1 = S.fr_rx1[lo];
             int cs = 0, cl = 0;
-            for (int cx = rx0; cx <= rx1; cx++) {
-                const Slot sl = T.slots[row + cx];
-                if (sl.child >= 0 && sl.count > kDescendMin) {
-                    add_range(S, cs, cl);
-                    cl = 0;
-                    int k = atomicAdd(&S.nstack, 1);
-                    if (k < kStackMax) {
-                        S.stack[k] = sl.child;
-                    } else {
-                        atomicSub(&S.nstack, 1);
-                        add_range(S, sl.start, sl.count);
+            for (int cx0 = rx0; cx0 <= rx1; cx0 += 4) {
+                Slot sl[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (cx0 + u <= rx1) sl[u] = T.slots[row + cx0 + u];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    if (cx0 + u > rx1) break;
+                    if (sl[u].child >= 0 && sl[u].count > kDescendMin) {
+                        add_range(S, cs, cl);
+                        cl = 0;
+                        const int k = atomicAdd(&S.nnext, 1);
+                        if (k < kFrontMax) S.front[cur ^ 1][k] = sl[u].child;
+                        else add_range(S, sl[u].start, sl[u].count);  // whole sub-tree
+                    } else if (sl[u].count > 0) {
+                        if (cl == 0) cs = sl[u].start;
+                        cl = sl[u].start + sl[u].count - cs;
                     }
-                } else if (sl.count > 0) {
-                    if (cl == 0) cs = sl.start;
-                    cl = sl.start + sl.count - cs;
                 }
             }
             add_range(S, cs, cl);
         }
-        __syncwarp();
+        __syncthreads();
+        if (tid == 0) {
+            S.nfront = min(S.nnext, kFrontMax);
+            S.nnext = 0;
+        }
+        cur ^= 1;
+        __syncthreads();
     }
-    __syncwarp();
     if (S.range_ovf) {
-        // Too many ranges: replace the list by the one range that covers them
-        // all (a superset, and no particle appears twice).
-        int lo = S.ovf_lo, hi = S.ovf_hi;
-        for (int r = lane; r < kRangeMax - 1; r += 32) {
-            const int2 rg = S.ranges[r];
-            lo = min(lo, rg.x);
-            hi = max(hi, rg.x + rg.y);
+        // Too many jobs: replace them by the one range that covers them all
+        // (a superset, and no particle appears twice).
+        if (tid < 32) {
+            int lo = S.ovf_lo, hi = S.ovf_hi;
+            const int nj = min(S.jfail, kJobMax);
+            for (int r = tid; r < nj; r += 32) {
+                const int2 jb = S.jobs[r];
+                lo = min(lo, jb.x);
+                hi = max(hi, jb.x + jb.y);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                lo = min(lo, __shfl_xor_sync(~0u, lo, o));
+                hi = max(hi, __shfl_xor_sync(~0u, hi, o));
+            }
+            if (tid == 0) {
+                S.jobs[0] = make_int2(lo, hi - lo);
+                S.njobs = (hi - lo + 31) >> 5;
+                S.cover = 1;
+                atomicOr(&T.ctr->status, kStWalk);
+            }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            lo = min(lo, __shfl_xor_sync(~0u, lo, o));
-            hi = max(hi, __shfl_xor_sync(~0u, hi, o));
-        }
-        __syncwarp();
-        if (lane == 0) {
-            S.ranges[0] = make_int2(lo, hi - lo);
-            S.nrange = 1;
-            atomicOr(&T.ctr->status, kStWalk);
-        }
+        __syncthreads();
     }
-    __syncwarp();
 }
 
-// Stream the candidates of the collected ranges.  mode 0: collect those with
+// Stream the candidates of the collected jobs.  mode 0: collect those with
 // original index in [wlo, whi) into the buffer; mode 1: histogram them into
 // 256 bins of width W starting at wlo.
 template <bool DENS>
@@ -199,43 +268,63 @@ __device__ void group_gather(const FindArgs &A, FindSmem &S, int mode, int wlo, 
     const float PL0 = S.box[0], PL1 = S.box[1], PL2 = S.box[2];
     const float PH0 = S.box[3], PH1 = S.box[4], PH2 = S.box[5];
     const float T2 = S.box[12];
-    const int gstart = S.gstart, gcount = S.gcount;
+    const int njobs = S.njobs;
+    const bool cover = S.cover;
+    const int2 cv = S.jobs[0];
+    const unsigned lt = (1u << lane) - 1;
     int kmin = INT_MAX, kmax = INT_MIN;
-    const int nr = S.nrange;
-    for (int r = warp; r < nr; r += 4) {
-        const int2 rg = S.ranges[r];
-        for (int off = 0; off < rg.y; off += 32) {
-            const int t = rg.x + off + lane;
-            bool keep = false;
-            float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-            int orig = 0;
-            if (off + lane < rg.y) {
-                c = __ldg(&A.T.spos[t]);
-                orig = __float_as_int(c.w);
-                float ex = fmaxf(fmaxf(__fsub_rn(PL0, c.x), __fsub_rn(c.x, PH0)), 0.0f);
-                float ey = fmaxf(fmaxf(__fsub_rn(PL1, c.y), __fsub_rn(c.y, PH1)), 0.0f);
-                float ez = fmaxf(fmaxf(__fsub_rn(PL2, c.z), __fsub_rn(c.z, PH2)), 0.0f);
-                float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-                keep = d2 <= T2 && orig >= wlo && orig < whi;
+    for (int j0 = warp * kUnroll; j0 < njobs; j0 += kFindWarps * kUnroll) {
+        float4 c[kUnroll];
+        float mm[kUnroll];
+        bool keep[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const int job = j0 + u;
+            int t = 0;
+            bool ok = false;
+            if (job < njobs) {
+                const int2 jb = cover ? make_int2(cv.x + 32 * job, min(32, cv.y - 32 * job)) : S.jobs[job];
+                ok = lane < jb.y;
+                t = jb.x + lane;
             }
+            c[u] = ok ? __ldg(&A.T.spos[t]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (DENS) mm[u] = ok ? __ldg(&A.smass[t]) : 0.0f;
+            keep[u] = ok;
+        }
+        unsigned bal[kUnroll];
+        int tot = 0;
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const int orig = __float_as_int(c[u].w);
+            const float ex = fmaxf(fmaxf(__fsub_rn(PL0, c[u].x), __fsub_rn(c[u].x, PH0)), 0.0f);
+            const float ey = fmaxf(fmaxf(__fsub_rn(PL1, c[u].y), __fsub_rn(c[u].y, PH1)), 0.0f);
+            const float ez = fmaxf(fmaxf(__fsub_rn(PL2, c[u].z), __fsub_rn(c[u].z, PH2)), 0.0f);
+            const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+            keep[u] = keep[u] && d2 <= T2 && orig >= wlo && orig < whi;
             if (mode == 0) {
-                const unsigned bal = __ballot_sync(~0u, keep);
-                if (bal == 0) continue;
-                int base = 0;
-                if (lane == 0) base = atomicAdd(&S.ncand, __popc(bal));
-                base = __shfl_sync(~0u, base, 0);
-                if (keep) {
-                    const int slot = base + __popc(bal & ((1u << lane) - 1));
+                bal[u] = __ballot_sync(~0u, keep[u]);
+                tot += __popc(bal[u]);
+            } else if (keep[u]) {
+                atomicAdd(&S.hist[(int)((unsigned)(orig - wlo) / (unsigned)W)], 1);
+            }
+        }
+        if (mode == 0 && tot > 0) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&S.ncand, tot);
+            base = __shfl_sync(~0u, base, 0);
+#pragma unroll
+            for (int u = 0; u < kUnroll; u++) {
+                if (keep[u]) {
+                    const int slot = base + __popc(bal[u] & lt);
                     if (slot < kCap) {
-                        S.cand[slot] = c;
-                        if (DENS) S.cmass[slot] = __ldg(&A.smass[t]);
-                        if (t >= gstart && t < gstart + gcount) S.qself[t - gstart] = slot;
+                        S.cand[slot] = c[u];
+                        if (DENS) S.cmass[slot] = mm[u];
                     }
+                    const int orig = __float_as_int(c[u].w);
                     kmin = min(kmin, orig);
                     kmax = max(kmax, orig);
                 }
-            } else if (keep) {
-                atomicAdd(&S.hist[(int)((unsigned)(orig - wlo) / (unsigned)W)], 1);
+                base += __popc(bal[u]);
             }
         }
     }
@@ -253,12 +342,39 @@ __device__ void group_gather(const FindArgs &A, FindSmem &S, int mode, int wlo, 
 
 __device__ __forceinline__ float m4_shape(float q)
 {
-    if (q < 1.0f) return fmaf(q * q, fmaf(0.75f, q, -1.5f), 1.0f);
-    if (q < 2.0f) {
-        float t = 2.0f - q;
-        return 0.25f * t * t * t;
+    const float t = 2.0f - q;
+    const float w2 = 0.25f * t * t * t;
+    const float w1 = fmaf(q * q, fmaf(0.75f, q, -1.5f), 1.0f);
+    return q < 1.0f ? w1 : (q < 2.0f ? w2 : 0.0f);
+}
+
+template <int E>
+__device__ __forceinline__ void sort_keys(uint32_t *buf)
+{
+    block_sort<kSortThreads, E>(buf);
+}
+
+// One FP32 filter step of stage A: the ballot of hits of query P over this
+// lane's candidate Q, and whether the pair lies in the uncertain band.
+__device__ __forceinline__ unsigned test_chunk(const float4 &P, float rhi, const float4 &Q,
+                                               bool valid, bool &amb)
+{
+    const float dx = Q.x - P.x, dy = Q.y - P.y, dz = Q.z - P.z;
+    const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    const bool hit = valid && d2 < P.w;
+    amb |= valid && !hit && d2 <= rhi;
+    return __ballot_sync(~0u, hit);
+}
+
+__device__ __forceinline__ void fix_band(FindSmem &S, int c, int gcount, const float4 &Q, int lane)
+{
+    for (int p = 0; p < gcount; p++) {
+        const float4 P = S.q[p];
+        const float dx = Q.x - P.x, dy = Q.y - P.y, dz = Q.z - P.z;
+        const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        if (!(d2 < P.w) && d2 <= S.qrhi[p] && exact_neighbor(P, S.qh[p], Q))
+            atomicOr(&S.mask[p * kChunks + c], 1u << lane);
     }
-    return 0.0f;
 }
 
 // Sort, test and emit the candidates of the current window.
@@ -270,61 +386,76 @@ __device__ void group_window(const FindArgs &A, FindSmem &S)
     const int gcount = S.gcount;
     if (m == 0) return;
     const int kmin = S.kmin;
-    int npad = 128;
+    int npad = kSortThreads;
     while (npad < m) npad <<= 1;
-    for (int s = tid; s < npad; s += 128) {
+    for (int s = tid; s < npad; s += kFindThreads) {
         uint32_t k = 0xffffffffu;
         if (s < m) k = ((uint32_t)(__float_as_int(S.cand[s].w) - kmin) << kSlotBits) | (uint32_t)s;
         S.key[s] = k;
     }
     __syncthreads();
-    block_sort_n(S.key, npad);
-    for (int k = tid; k < m; k += 128) S.rank_of[S.key[k] & (kCap - 1)] = (unsigned short)k;
+    if (tid < kSortThreads) {
+        switch (npad) {
+        case kSortThreads: sort_keys<1>(S.key); break;
+        case 2 * kSortThreads: sort_keys<2>(S.key); break;
+        case 4 * kSortThreads: sort_keys<4>(S.key); break;
+        default: sort_keys<8>(S.key); break;
+        }
+    }
     __syncthreads();
+    // sorted position of each query itself (it is its own candidate when its
+    // original index lies in this window)
+    if (tid < gcount) {
+        const int o = S.qorig[tid];
+        const uint32_t want = (uint32_t)(o - kmin);
+        int lo = 0, hi = m;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((S.key[mid] >> kSlotBits) < want) lo = mid + 1; else hi = mid;
+        }
+        S.qself[tid] = (o >= kmin && lo < m && (S.key[lo] >> kSlotBits) == want) ? lo : -1;
+    }
 
-    // ---- stage A: one ballot per (query, chunk)
+    // ---- stage A: one ballot per (query, chunk); two chunks per pass
     const int nch = (m + 31) >> 5;
-    for (int c = warp; c < nch; c += 4) {
-        const int k = c * 32 + lane;
-        const bool valid = k < m;
-        float4 Q = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (valid) Q = S.cand[S.key[k] & (kCap - 1)];
-        bool amb = false;
+    for (int c = warp; c < nch; c += 2 * kFindWarps) {
+        const int c2 = c + kFindWarps;
+        const bool has2 = c2 < nch;
+        const int k1 = c * 32 + lane, k2 = c2 * 32 + lane;
+        const bool v1 = k1 < m, v2 = k2 < m;
+        float4 Q1 = make_float4(0.f, 0.f, 0.f, 0.f), Q2 = Q1;
+        if (v1) Q1 = S.cand[S.key[k1] & (kCap - 1)];
+        if (v2) Q2 = S.cand[S.key[k2] & (kCap - 1)];
+        bool amb1 = false, amb2 = false;
         for (int p = 0; p < gcount; p++) {
             const float4 P = S.q[p];
             const float rhi = S.qrhi[p];
-            const float dx = Q.x - P.x, dy = Q.y - P.y, dz = Q.z - P.z;
-            const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const bool hit = valid && d2 < P.w;
-            amb |= valid && !hit && d2 <= rhi;
-            const unsigned bal = __ballot_sync(~0u, hit);
-            if (lane == 0) S.mask[p * kChunks + c] = bal;
+            const unsigned b1 = test_chunk(P, rhi, Q1, v1, amb1);
+            const unsigned b2 = test_chunk(P, rhi, Q2, v2, amb2);
+            if (lane == 0) {
+                S.mask[p * kChunks + c] = b1;
+                if (has2) S.mask[p * kChunks + c2] = b2;
+            }
         }
         __syncwarp();
-        if (__any_sync(~0u, amb)) {
-            if (amb) {
-                for (int p = 0; p < gcount; p++) {
-                    const float4 P = S.q[p];
-                    const float rhi = S.qrhi[p];
-                    const float dx = Q.x - P.x, dy = Q.y - P.y, dz = Q.z - P.z;
-                    const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    if (!(d2 < P.w) && d2 <= rhi && exact_neighbor(P, S.qh[p], Q))
-                        atomicOr(&S.mask[p * kChunks + c], 1u << lane);
-                }
-            }
+        if (__any_sync(~0u, amb1)) {
+            if (amb1) fix_band(S, c, gcount, Q1, lane);
+            __syncwarp();
+        }
+        if (__any_sync(~0u, amb2)) {
+            if (amb2) fix_band(S, c2, gcount, Q2, lane);
             __syncwarp();
         }
     }
     __syncthreads();
 
-    // ---- stage B: ascending rows by prefix sums of the ballots
-    for (int p = warp; p < gcount; p += 4) {
+    // ---- stage B: per query, compact the ballots into hit positions, then
+    // write the row (and the density terms) lane-parallel in ascending order.
+    unsigned short *hl = S.hits[warp];
+    for (int p = warp; p < gcount; p += kFindWarps) {
         uint32_t mk = lane < nch ? S.mask[p * kChunks + lane] : 0u;
-        const int self = S.qself[p];
-        if (self >= 0) {
-            const int sr = S.rank_of[self];
-            if (lane == (sr >> 5)) mk &= ~(1u << (sr & 31));
-        }
+        const int sr = S.qself[p];
+        if (sr >= 0 && lane == (sr >> 5)) mk &= ~(1u << (sr & 31));
         const int cnt = __popc(mk);
         int incl = cnt;
         for (int o = 1; o < 32; o <<= 1) {
@@ -332,42 +463,62 @@ __device__ void group_window(const FindArgs &A, FindSmem &S)
             if (lane >= o) incl += t;
         }
         const int total = __shfl_sync(~0u, incl, 31);
-        int pos = S.qcnt[p] + incl - cnt;
+        const int excl = incl - cnt;
+        const int base = S.qcnt[p];
         int32_t *row = A.nbrs + (long long)S.qorig[p] * A.ngmax;
         const float4 P = S.q[p];
-        const float inv_h = 1.0f / S.qh[p];
-        float acc = 0.0f;
-        while (mk) {
-            const int bit = __ffs(mk) - 1;
-            mk &= mk - 1;
-            const uint32_t key = S.key[lane * 32 + bit];
-            if (pos < A.ngmax) row[pos] = kmin + (int)(key >> kSlotBits);
-            pos++;
-            if (DENS) {
-                const int slot = key & (kCap - 1);
-                const float4 Q = S.cand[slot];
-                const float dx = Q.x - P.x, dy = Q.y - P.y, dz = Q.z - P.z;
-                const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                acc = fmaf(S.cmass[slot], m4_shape(sqrtf(d2) * inv_h), acc);
+        const float inv_h = DENS ? __frcp_rn(S.qh[p]) : 0.0f;
+        // lane L takes the list positions congruent to L mod 32 and continues
+        // its slot of the running density sum
+        const int i0 = (lane - base) & 31;
+        float acc = DENS ? S.qacc[p][lane] : 0.0f;
+        for (int b0 = 0; b0 < total; b0 += kHitBatch) {
+            if (total <= kHitBatch) {
+                uint32_t mm = mk;
+                int r = excl;
+                while (mm) {
+                    hl[r++] = (unsigned short)(lane * 32 + __ffs(mm) - 1);
+                    mm &= mm - 1;
+                }
+            } else if (excl < b0 + kHitBatch && excl + cnt > b0) {
+                uint32_t mm = mk;
+                int r = excl;
+                while (mm) {
+                    const int bit = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    if (r >= b0 && r < b0 + kHitBatch) hl[r - b0] = (unsigned short)(lane * 32 + bit);
+                    r++;
+                }
             }
+            __syncwarp();
+            const int nb = min(kHitBatch, total - b0);
+            for (int i = i0; i < nb; i += 32) {
+                const uint32_t key = S.key[hl[i]];
+                const int pos = base + b0 + i;
+                if (pos < A.ngmax) row[pos] = kmin + (int)(key >> kSlotBits);
+                if (DENS) {
+                    const int slot = key & (kCap - 1);
+                    const float4 Q = S.cand[slot];
+                    const float dx = Q.x - P.x, dy = Q.y - P.y, dz = Q.z - P.z;
+                    const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    const float q = d2 > 0.0f ? d2 * rsqrtf(d2) * inv_h : 0.0f;
+                    acc = fmaf(S.cmass[slot], m4_shape(q), acc);
+                }
+            }
+            __syncwarp();
         }
-        if (DENS) {
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(~0u, acc, o);
-        }
-        if (lane == 0) {
-            S.qcnt[p] += total;
-            if (DENS) S.qacc[p] += acc;
-        }
+        if (DENS) S.qacc[p][lane] = acc;
+        if (lane == 0) S.qcnt[p] = base + total;
     }
     __syncthreads();
 }
 
 template <bool DENS>
-__global__ void __launch_bounds__(128) k_find(FindArgs A)
+__global__ void __launch_bounds__(kFindThreads, 4) k_find(FindArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FindSmem &S = *reinterpret_cast<FindSmem *>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const TreeDev &T = A.T;
     const int nchunks = (A.ngroups + kFindChunk - 1) / kFindChunk;
 
@@ -375,9 +526,12 @@ __global__ void __launch_bounds__(128) k_find(FindArgs A)
         const int g1 = min(chunk * kFindChunk + kFindChunk, A.ngroups);
         for (int g = chunk * kFindChunk; g < g1; g++) {
             __syncthreads();
-            const int2 grp = T.groups[g];
-            // ---- queries (warp 0)
+            if (DENS)
+                for (int i = tid; i < kGroupMax * 32; i += kFindThreads) (&S.qacc[0][0])[i] = 0.0f;
+            // ---- queries (warp 0), FP32 only: RN(2h * 2h) is the float
+            // rounding of the exact binary64 (2h)^2.
             if (tid < 32) {
+                const int2 grp = T.groups[g];
                 const bool v = lane < grp.y;
                 float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
                 float h = 0.0f;
@@ -385,22 +539,20 @@ __global__ void __launch_bounds__(128) k_find(FindArgs A)
                     r = T.spos[grp.x + lane];
                     h = T.sh[grp.x + lane];
                 }
-                const double two_h = __dmul_rn(2.0, (double)h);
-                const double R64 = __dmul_rn(two_h, two_h);
-                float rlo = -1.0f, rhi = FLT_MAX;
-                if (R64 >= 0x1p-100 && R64 <= 0x1p100) {
-                    const float r32 = __double2float_rn(R64);
+                const float two_h = 2.0f * h;
+                const float r32 = __fmul_rn(two_h, two_h);
+                float rlo = -1.0f, rhi = __int_as_float(0x7f800000);
+                if (r32 >= 0x1p-100f && r32 <= 0x1p100f) {
                     rlo = __fmul_rd(r32, 1.0f - 0x1p-18f);
                     rhi = __fmul_ru(r32, 1.0f + 0x1p-18f);
                 }
-                const float rs = __fmul_ru(__fmul_ru(h, 2.0f), 1.0f + 0x1p-20f);
+                const float rs = __fmul_ru(two_h, 1.0f + 0x1p-20f);
                 if (v) {
                     S.q[lane] = make_float4(r.x, r.y, r.z, rlo);
                     S.qrhi[lane] = rhi;
                     S.qh[lane] = h;
                     S.qorig[lane] = __float_as_int(r.w);
                     S.qcnt[lane] = 0;
-                    S.qacc[lane] = 0.0f;
                 }
                 const float big = FLT_MAX;
                 float pl0 = v ? r.x : big, pl1 = v ? r.y : big, pl2 = v ? r.z : big;
@@ -424,10 +576,9 @@ __global__ void __launch_bounds__(128) k_find(FindArgs A)
                     S.gstart = grp.x;
                     S.gcount = grp.y;
                 }
-                __syncwarp();
-                group_walk(T, S, lane);
             }
             __syncthreads();
+            group_walk(T, S);
 
             // ---- windows over original index
             int wlo = 0;
@@ -438,7 +589,6 @@ __global__ void __launch_bounds__(128) k_find(FindArgs A)
                     S.kmin = INT_MAX;
                     S.kmax = INT_MIN;
                 }
-                if (tid < kGroupMax) S.qself[tid] = -1;
                 __syncthreads();
                 group_gather<DENS>(A, S, 0, wlo, whi, 1);
                 __syncthreads();
@@ -449,7 +599,7 @@ __global__ void __launch_bounds__(128) k_find(FindArgs A)
                     if (tid == 0) atomicOr(&T.ctr->status, kStWalk);
                     for (;;) {
                         const int Wd = (int)((span + 255) / 256);
-                        for (int i = tid; i < 256; i += 128) S.hist[i] = 0;
+                        for (int i = tid; i < 256; i += kFindThreads) S.hist[i] = 0;
                         __syncthreads();
                         group_gather<DENS>(A, S, 1, wlo, (int)min((long long)INT_MAX, wlo + span), Wd);
                         __syncthreads();
@@ -475,7 +625,6 @@ __global__ void __launch_bounds__(128) k_find(FindArgs A)
                         S.kmin = INT_MAX;
                         S.kmax = INT_MIN;
                     }
-                    if (tid < kGroupMax) S.qself[tid] = -1;
                     __syncthreads();
                     group_gather<DENS>(A, S, 0, wlo, whi, 1);
                     __syncthreads();
@@ -488,13 +637,18 @@ __global__ void __launch_bounds__(128) k_find(FindArgs A)
             // ---- results
             if (tid < S.gcount) {
                 const int c = S.qcnt[tid];
-                const int o = S.qorig[tid];
-                A.counts[o] = c;
+                A.counts[S.qorig[tid]] = c;
                 if (c > A.ngmax) atomicOr(&T.ctr->status, kStNgmax);
-                if (DENS) {
-                    const float h = S.qh[tid];
-                    const float mp = A.smass[S.gstart + tid];
-                    A.rho[o] = (mp + S.qacc[tid]) / (kPiF * h * h * h);
+            }
+            if (DENS) {
+                for (int p = warp; p < S.gcount; p += kFindWarps) {
+                    float a = S.qacc[p][lane];
+                    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(~0u, a, o);
+                    if (lane == 0) {
+                        const float hh = S.qh[p];
+                        const float mp = A.smass[S.gstart + p];
+                        A.rho[S.qorig[p]] = (mp + a) / (kPiF * hh * hh * hh);
+                    }
                 }
             }
         }
@@ -536,19 +690,21 @@ cudaError_t launch_find(const TreeDev &T, int ngroups, int ngmax, int32_t *nbrs,
     if (dens) {
         int nb = (T.n + 255) / 256;
         if (nb > sms * 8) nb = sms * 8;
+        note_launch();
         k_mass_to_tree<<<nb, 256, 0, st>>>(T.spos, m, smass, T.n);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_find<true>, 128, sizeof(FindSmem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_find<true>, kFindThreads, sizeof(FindSmem));
     } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_find<false>, 128, sizeof(FindSmem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_find<false>, kFindThreads, sizeof(FindSmem));
     }
     if (per_sm < 1) per_sm = 1;
     long long nchunks = (ngroups + kFindChunk - 1) / kFindChunk;
     long long blocks = (long long)sms * per_sm;
     if (blocks > nchunks) blocks = nchunks;
+    note_launch();
     if (dens)
-        k_find<true><<<(int)blocks, 128, sizeof(FindSmem), st>>>(A);
+        k_find<true><<<(int)blocks, kFindThreads, sizeof(FindSmem), st>>>(A);
     else
-        k_find<false><<<(int)blocks, 128, sizeof(FindSmem), st>>>(A);
+        k_find<false><<<(int)blocks, kFindThreads, sizeof(FindSmem), st>>>(A);
     return cudaGetLastError();
 }
 
@@ -565,7 +721,7 @@ __global__ void __launch_bounds__(256) k_density(TreeDev T, const float *__restr
         const int ti = T.inv[i];
         const float4 P = T.spos[ti];
         const float h = T.sh[ti];
-        const float inv_h = 1.0f / h;
+        const float inv_h = __frcp_rn(h);
         const int c = min(counts[i], ngmax);
         const int32_t *row = nbrs + (long long)i * ngmax;
         float acc = 0.0f;
@@ -574,7 +730,8 @@ __global__ void __launch_bounds__(256) k_density(TreeDev T, const float *__restr
             const float4 Q = T.spos[T.inv[j]];
             const float dx = Q.x - P.x, dy = Q.y - P.y, dz = Q.z - P.z;
             const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            acc = fmaf(m[j], m4_shape(sqrtf(d2) * inv_h), acc);
+            const float q = d2 > 0.0f ? d2 * rsqrtf(d2) * inv_h : 0.0f;
+            acc = fmaf(m[j], m4_shape(q), acc);
         }
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(~0u, acc, o);
         if (lane == 0) rho[i] = (m[i] + acc) / (kPiF * h * h * h);
@@ -587,6 +744,7 @@ cudaError_t launch_density(const TreeDev &T, const float *m, const int32_t *nbrs
     if (T.n <= 0) return cudaSuccess;
     long long blocks = ((long long)T.n + 7) / 8;
     if (blocks > sms * 16) blocks = sms * 16;
+    note_launch();
     k_density<<<(int)blocks, 256, 0, st>>>(T, m, nbrs, counts, ngmax, rho);
     return cudaGetLastError();
 }

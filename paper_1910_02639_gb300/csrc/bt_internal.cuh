@@ -9,8 +9,12 @@
 
 namespace bt {
 
+// Host-side count of kernel launches (defined in bt_api.cu).
+void note_launch(int k = 1);
+
 constexpr int kDepthMax = 32;   // a cell at depth 32 is never split
-constexpr int kGroupMax = 32;   // particles per find work unit (one per lane)
+constexpr int kGroupMax = 32;   // particles per find work unit
+constexpr int kWholeMax = 32;   // cells up to this size become one work unit
 constexpr int kSmallCap = 256;  // cells up to this size are built by one warp in smem
 constexpr int kBigChunk = 4096; // particles per block in the per-level big-cell passes
 
@@ -73,12 +77,14 @@ __device__ __forceinline__ int coord_fp64(float x, double lo, double hi, int b)
     return (int)f;
 }
 
-// Eq. 2 with an FP32 fast path.  v32 = fl32(fl32(x - lo32) * scale32) differs
-// from the binary64 value v by at most E = 2^-22 (|v32| + |lo| s) +
-// 2^-147 (s + 1), s = b/(hi-lo) (three float roundings of relative size
-// 2^-24 on the value and on lo, plus underflow; cn holds the constant part
-// rounded up).  If v32 is farther than E from every integer, floor(v32) =
-// floor(v); otherwise the binary64 definition decides.
+// Eq. 2 with an FP32 fast path.  v32 = fl32(fl32(x - lo32) * scale32) with
+// scale32 = fl32(b / fl32(hi - lo)) differs from the binary64 value v by at
+// most E = 2^-21 (|v32| + |lo| s) + 2^-146 (s + 1), s = b/(hi-lo): the scale
+// carries two float roundings, the subtraction, the product and lo32 one
+// each (relative 2^-24), binary64 adds 4 * 2^-53, underflow an absolute
+// 2^-149 per step; cn holds the constant part rounded up.  If v32 is farther
+// than E from every integer, floor(v32) = floor(v); otherwise the binary64
+// definition decides.
 __device__ __forceinline__ int coord_fast(float x, const NodeWalk &w, const NodeGeom &g,
                                           int l, int b)
 {
@@ -87,7 +93,7 @@ __device__ __forceinline__ int coord_fast(float x, const NodeWalk &w, const Node
         float v = __fmul_rn(__fsub_rn(x, w.lo[l]), w.scale[l]);
         float av = fabsf(v);
         if (av < 4194304.0f) {  // 2^22: fractional part exact
-            float e = __fmaf_ru(av, 0x1p-22f, w.cn[l]);
+            float e = __fmaf_ru(av, 0x1p-21f, w.cn[l]);
             float k = floorf(v);
             if (__fsub_rn(v, k) > e && __fsub_rn(k + 1.0f, v) > e) {
                 int c = (int)k;
@@ -111,8 +117,8 @@ __device__ __forceinline__ void walk_range(float ql, float qh, const NodeWalk &w
     // same operation sequence as coord_fast, so the same bound E applies
     float vl = __fmul_rn(__fsub_rn(ql, w.lo[l]), w.scale[l]);
     float vh = __fmul_rn(__fsub_rn(qh, w.lo[l]), w.scale[l]);
-    float el = __fmaf_ru(fabsf(vl), 0x1p-22f, w.cn[l]);
-    float eh = __fmaf_ru(fabsf(vh), 0x1p-22f, w.cn[l]);
+    float el = __fmaf_ru(fabsf(vl), 0x1p-21f, w.cn[l]);
+    float eh = __fmaf_ru(fabsf(vh), 0x1p-21f, w.cn[l]);
     float fl = floorf(__fsub_rd(vl, el));
     float fh = floorf(__fadd_ru(vh, eh));
     // clamp in float first (also maps NaN to the full range)
@@ -142,34 +148,59 @@ __device__ __forceinline__ void make_walk(const NodeGeom &g, int b, int slot0, N
             w.cn[l] = 0.0f;
             continue;
         }
-        double s = __ddiv_rn((double)b, width);
-        double alo = fabs(g.lo[l]);
-        if (!(s < 1e30) || !(alo < 1e30)) {
+        // FP32 scale (binary64 division is slow on this GPU); its rounding is
+        // part of the bound documented at coord_fast.
+        const float wid32 = __double2float_rn(width);
+        const float alo = fabsf(w.lo[l]);
+        if (!(wid32 > 0x1p-100f) || !(wid32 < 0x1p100f) || !(alo < 0x1p100f)) {
             w.flags |= kFlagWide;
             w.scale[l] = 0.0f;
             w.cn[l] = 0.0f;
             continue;
         }
-        w.scale[l] = __double2float_rn(s);
-        double c = 0x1p-22 * (alo * s + 1.0) + 0x1p-147 * (s + 1.0);
-        w.cn[l] = __double2float_ru(c * (1.0 + 0x1p-40));
+        const float s32 = __fdiv_rn((float)b, wid32);
+        w.scale[l] = s32;
+        const float s_up = __fmul_ru(s32, 1.0f + 0x1p-20f);     // >= b/(hi-lo)
+        const float alo_up = __fmul_ru(alo, 1.0f + 0x1p-22f);   // >= |lo|
+        float c = __fmaf_ru(__fmul_ru(alo_up, s_up), 0x1p-21f, 0x1p-21f);
+        c = __fmaf_ru(__fadd_ru(s_up, 1.0f), 0x1p-126f, c);     // covers 2^-146 (s + 1)
+        w.cn[l] = c;
     }
 }
 
-// Child box of sub-cell coordinate c in one dimension (Sec. 3.1 step 2,
-// equal-size sub-cells), binary64 in the oracle's operation order.
-__device__ __forceinline__ void child_bounds(double lo, double hi, int b, int c,
-                                             double &clo, double &chi)
+// Sub-cell width w = (hi - lo)/b of one dimension, binary64.
+__device__ __forceinline__ double cell_width(double lo, double hi, int b)
 {
-    double w = __ddiv_rn(__dsub_rn(hi, lo), (double)b);
+    return __ddiv_rn(__dsub_rn(hi, lo), (double)b);
+}
+
+// Child box of sub-cell coordinate c in one dimension (Sec. 3.1 step 2,
+// equal-size sub-cells), binary64 in the oracle's operation order, given the
+// cell width w from cell_width.
+__device__ __forceinline__ void child_bounds_w(double lo, double hi, double w, int b, int c,
+                                               double &clo, double &chi)
+{
     clo = __dadd_rn(lo, __dmul_rn((double)c, w));
     chi = (c == b - 1) ? hi : __dadd_rn(lo, __dmul_rn((double)(c + 1), w));
 }
 
-// Eq. 1 in integers: smallest b >= 2 with b^3 s >= n.
+__device__ __forceinline__ void child_bounds(double lo, double hi, int b, int c,
+                                             double &clo, double &chi)
+{
+    child_bounds_w(lo, hi, cell_width(lo, hi, b), b, c, clo, chi);
+}
+
+// Largest number of underfull sub-cells at which branching factor b is
+// accepted (Eq. 4: halve iff u > beta*b^3 in binary64), tabulated per b on
+// the host for the tree's beta.
+constexpr int kMaxB = 1300;
+
+// Eq. 1 in integers: smallest b >= 2 with b^3 s >= n.  A float cube root
+// gives the starting point, exact integer tests settle it (no binary64 math:
+// it is slow on this GPU).
 __device__ __host__ __forceinline__ int branching_factor(long long n, long long s)
 {
-    long long b = (long long)cbrt((double)n / (double)s);
+    long long b = (long long)cbrtf((float)n / (float)s);
     if (b < 2) b = 2;
     while (b > 2 && (b - 1) * (b - 1) * (b - 1) * s >= n) b--;
     while (b * b * b * s < n) b++;
@@ -213,7 +244,12 @@ struct BigCell {
     int chunk_base;    // first kBigChunk block of this cell
     int state;         // 0 pending, 1 accepted, 2 stays a leaf
     int slot0;
+    int u;             // sub-cells with n_j <= alpha s (current b)
+    int ne;            // non-empty sub-cells
+    int lastj;         // largest non-empty sub-cell id
+    int halved;        // b was just halved: histogram to clear
     int pad;
+    double w[3];       // sub-cell widths (hi - lo)/b of the accepted b
 };
 
 struct SmallItem {
@@ -229,6 +265,7 @@ struct TreeDev {
     NodeWalk *walk;
     Slot *slots;
     int2 *groups;
+    const int *halve_thr;  // [kMaxB+1]: accept b iff u <= halve_thr[b]
     float4 *spos;   // tree order: x, y, z, orig index (bits)
     float *sh;      // tree order: h
     int *inv;       // inverse permutation: tree position of original index

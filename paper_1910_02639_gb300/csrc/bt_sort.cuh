@@ -1,5 +1,5 @@
 // bt_sort.cuh -- block-wide bitonic sort of unique 32-bit keys held in
-// registers (E keys per thread, 128 threads, N = 128*E), used to put a work
+// registers (E keys per thread, NT threads, N = NT*E), used to put a work
 // unit's candidate particles in ascending original-index order.
 //
 // Every comparator is ascending: merge step k first compares element i with
@@ -12,7 +12,15 @@
 
 namespace bt {
 
-constexpr int kSortThreads = 128;
+// Barrier over the NT threads that take part in the sort (threads 0..NT-1 of
+// the block): __syncthreads when they are the whole block, else named
+// barrier 1.
+template <int NT>
+__device__ __forceinline__ void sort_barrier()
+{
+    if (NT == 0) return;
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
 
 template <int V>
 struct Log2 { static constexpr int value = 1 + Log2<V / 2>::value; };
@@ -22,7 +30,7 @@ struct Log2<1> { static constexpr int value = 0; };
 template <int V>
 struct HighBit { static constexpr int value = 1 << Log2<V>::value; };
 
-template <int E, int M>
+template <int NT, int E, int M>
 __device__ __forceinline__ void bsort_stage(uint32_t (&v)[E], uint32_t *buf)
 {
     constexpr int LE = Log2<E>::value;
@@ -47,10 +55,10 @@ __device__ __forceinline__ void bsort_stage(uint32_t (&v)[E], uint32_t *buf)
 #pragma unroll
             for (int r = 0; r < E; r++) x[r] = __shfl_xor_sync(0xffffffffu, v[r ^ MR], MT);
         } else {
-            __syncthreads();
+            sort_barrier<NT>();
 #pragma unroll
             for (int r = 0; r < E; r++) buf[threadIdx.x * E + r] = v[r];
-            __syncthreads();
+            sort_barrier<NT>();
             const int tp = threadIdx.x ^ MT;
 #pragma unroll
             for (int r = 0; r < E; r++) x[r] = buf[tp * E + (r ^ MR)];
@@ -60,48 +68,38 @@ __device__ __forceinline__ void bsort_stage(uint32_t (&v)[E], uint32_t *buf)
     }
 }
 
-template <int E, int J>
+template <int NT, int E, int J>
 __device__ __forceinline__ void bsort_inner(uint32_t (&v)[E], uint32_t *buf)
 {
     if constexpr (J >= 1) {
-        bsort_stage<E, J>(v, buf);
-        bsort_inner<E, J / 2>(v, buf);
+        bsort_stage<NT, E, J>(v, buf);
+        bsort_inner<NT, E, J / 2>(v, buf);
     }
 }
 
-template <int E, int K>
+template <int NT, int E, int K>
 __device__ __forceinline__ void bsort_outer(uint32_t (&v)[E], uint32_t *buf)
 {
-    if constexpr (K <= kSortThreads * E) {
-        bsort_stage<E, K - 1>(v, buf);   // mirror comparison
-        bsort_inner<E, K / 4>(v, buf);
-        bsort_outer<E, K * 2>(v, buf);
+    if constexpr (K <= NT * E) {
+        bsort_stage<NT, E, K - 1>(v, buf);   // mirror comparison
+        bsort_inner<NT, E, K / 4>(v, buf);
+        bsort_outer<NT, E, K * 2>(v, buf);
     }
 }
 
-// Sorts buf[0 .. 128*E) ascending in place.  All 128 threads must call it.
-template <int E>
+// Sorts buf[0 .. NT*E) ascending in place.  Threads 0..NT-1 of the block
+// must call it (others must not); it synchronises only them.
+template <int NT, int E>
 __device__ __forceinline__ void block_sort(uint32_t *buf)
 {
     uint32_t v[E];
 #pragma unroll
     for (int r = 0; r < E; r++) v[r] = buf[threadIdx.x * E + r];
-    bsort_outer<E, 2>(v, buf);
-    __syncthreads();
+    bsort_outer<NT, E, 2>(v, buf);
+    sort_barrier<NT>();
 #pragma unroll
     for (int r = 0; r < E; r++) buf[threadIdx.x * E + r] = v[r];
-    __syncthreads();
-}
-
-// Dispatch on the padded size (a power of two, 128 .. 128*8).
-__device__ __forceinline__ void block_sort_n(uint32_t *buf, int npad)
-{
-    switch (npad) {
-    case 128: block_sort<1>(buf); break;
-    case 256: block_sort<2>(buf); break;
-    case 512: block_sort<4>(buf); break;
-    default: block_sort<8>(buf); break;
-    }
+    sort_barrier<NT>();
 }
 
 }  // namespace bt
