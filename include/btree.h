@@ -148,6 +148,38 @@ int btree_find_neighbors_density(const btree_t *t, const float *m, int ngmax,
                                  float *rho, void *stream);
 
 /*
+ * btree_find_neighbors_density_noalloc -- btree_find_neighbors_density for
+ * callers that cannot allocate device memory when they search (a real-time
+ * loop that forbids allocation after set-up, a host framework that owns all
+ * device memory).  The paper has no counterpart: this is a deployment form
+ * of the same computation, with identical results.
+ *
+ * The fused search needs one scratch buffer (the masses in tree order,
+ * n floats).  btree_find_neighbors_density allocates it on first use; this
+ * entry point uses a fixed array compiled into the library instead and calls
+ * no allocator (no cudaMalloc/cudaFree, no allocating library routine).
+ *  - Limit: t's n must be <= btree_noalloc_max_particles() (2^21 = 2097152);
+ *    larger trees are rejected with BT_ERR_CAPACITY before any GPU work.
+ *  - The array (8 MB) lives on every GPU that loads the library until the
+ *    process exits.
+ *  - The first call on a device looks up the array's device address (once
+ *    per device, with that device current); make that first call before any
+ *    CUDA stream capture.
+ *  - All calls share the one array: calls whose GPU work overlaps in time
+ *    (different streams, or different threads) race on it and may return
+ *    wrong densities.  Serialise them (same stream, or events).
+ * Arguments, outputs and the other errors are those of
+ * btree_find_neighbors_density.  The tree itself must already be built
+ * (btree_build allocates; do that during set-up).
+ */
+int btree_find_neighbors_density_noalloc(const btree_t *t, const float *m, int ngmax,
+                                         int32_t *neighbors, int32_t *counts,
+                                         float *rho, void *stream);
+
+/* Largest n accepted by btree_find_neighbors_density_noalloc. */
+int64_t btree_noalloc_max_particles(void);
+
+/*
  * sph_density -- the density sum above, computed from existing lists.
  *
  * Uses the first min(counts[i], ngmax) entries of row i (so rows truncated

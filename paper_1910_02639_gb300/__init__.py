@@ -18,7 +18,8 @@ import threading
 
 __all__ = [
     "BtreeError", "Tree", "btree_build", "btree_find_neighbors",
-    "btree_find_neighbors_density", "sph_density", "btree_status", "btree_get_info",
+    "btree_find_neighbors_density", "btree_find_neighbors_density_noalloc",
+    "btree_noalloc_max_particles", "sph_density", "btree_status", "btree_get_info",
     "btree_export", "btree_free", "btree_strerror", "btree_version", "btree_kernel_launches",
     "library_path",
     "BT_OK", "BT_WARN_NGMAX", "BT_WARN_OVERSIZED_LEAF",
@@ -76,6 +77,10 @@ def _load():
         lib.btree_find_neighbors.argtypes = [vp, ctypes.c_int, vp, vp, vp]
         lib.btree_find_neighbors_density.restype = ctypes.c_int
         lib.btree_find_neighbors_density.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp]
+        lib.btree_find_neighbors_density_noalloc.restype = ctypes.c_int
+        lib.btree_find_neighbors_density_noalloc.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp]
+        lib.btree_noalloc_max_particles.restype = ctypes.c_int64
+        lib.btree_noalloc_max_particles.argtypes = []
         lib.sph_density.restype = ctypes.c_int
         lib.sph_density.argtypes = [vp, vp, vp, vp, ctypes.c_int, vp, vp]
         lib.btree_status.restype = ctypes.c_int
@@ -188,6 +193,26 @@ def btree_find_neighbors_density(tree: Tree, m, ngmax: int, neighbors, counts, r
         _dptr(counts, torch.int32, "counts", n), _dptr(rho, torch.float32, "rho", n),
         ctypes.c_void_p(_stream_ptr(stream)))
     return _check(st, "btree_find_neighbors_density")
+
+
+def btree_find_neighbors_density_noalloc(tree: Tree, m, ngmax: int, neighbors, counts, rho,
+                                         stream=None) -> int:
+    """As btree_find_neighbors_density, for callers that cannot allocate
+    device memory when they search: the library's only scratch buffer for
+    this call is a fixed array compiled into it (trees of at most
+    btree_noalloc_max_particles() particles; concurrent calls race on it)."""
+    import torch
+    n = tree.n
+    st = _load().btree_find_neighbors_density_noalloc(
+        tree.handle, _dptr(m, torch.float32, "m", n), int(ngmax),
+        _dptr(neighbors, torch.int32, "neighbors", n * ngmax),
+        _dptr(counts, torch.int32, "counts", n), _dptr(rho, torch.float32, "rho", n),
+        ctypes.c_void_p(_stream_ptr(stream)))
+    return _check(st, "btree_find_neighbors_density_noalloc")
+
+
+def btree_noalloc_max_particles() -> int:
+    return int(_load().btree_noalloc_max_particles())
 
 
 def sph_density(tree: Tree, m, neighbors, counts, ngmax: int, rho, stream=None) -> int:

@@ -417,6 +417,19 @@ int btree_find_neighbors_density(const btree_t *tc, const float *m, int ngmax, i
                                  t->sms, st));
 }
 
+int btree_find_neighbors_density_noalloc(const btree_t *t, const float *m, int ngmax,
+                                         int32_t *neighbors, int32_t *counts, float *rho,
+                                         void *stream)
+{
+    if (!t || ngmax < 1 || (t->n > 0 && (!neighbors || !counts || !m || !rho))) return BT_ERR_ARG;
+    if (t->n > noalloc_max_particles()) return BT_ERR_CAPACITY;
+    if (t->n == 0) return BT_OK;
+    return to_status(launch_find_density_noalloc(view(t), t->ngroups, ngmax, neighbors, counts, m,
+                                                 rho, t->sms, static_cast<cudaStream_t>(stream)));
+}
+
+int64_t btree_noalloc_max_particles(void) { return noalloc_max_particles(); }
+
 int sph_density(const btree_t *t, const float *m, const int32_t *neighbors, const int32_t *counts,
                 int ngmax, float *rho, void *stream)
 {

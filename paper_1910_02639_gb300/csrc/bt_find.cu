@@ -29,6 +29,7 @@
 #include "bt_find.cuh"
 
 #include <cfloat>
+#include <mutex>
 
 namespace bt {
 
@@ -706,6 +707,57 @@ cudaError_t launch_find(const TreeDev &T, int ngroups, int ngmax, int32_t *nbrs,
     else
         k_find<false><<<(int)blocks, kFindThreads, sizeof(FindSmem), st>>>(A);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- no-alloc form
+// Some callers cannot allocate device memory at the point where they search
+// (an allocator-free real-time loop, a host framework that owns all memory
+// and forbids allocation after set-up).  For them the fused search keeps its
+// scratch -- the masses permuted to tree order -- in this file-scope array
+// instead of a buffer allocated on first use.  Every GPU that loads the
+// library holds it (8 MB) until the process exits.
+constexpr long long kNoAllocMaxN = 1LL << 21;
+static __device__ __align__(256) float g_noalloc_smass[kNoAllocMaxN];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+long long noalloc_max_particles() { return kNoAllocMaxN; }
+
+// Device address of the static scratch array on the current device, looked
+// up once per device (a host-side name of a __device__ array is not a device
+// address).  The first call on a device does the look-up.
+static cudaError_t noalloc_scratch(float **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        float *p = nullptr;
+        e = cudaGetSymbolAddress((void **)&p, g_noalloc_smass);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t launch_find_density_noalloc(const TreeDev &T, int ngroups, int ngmax, int32_t *nbrs,
+                                        int32_t *counts, const float *m, float *rho, int sms,
+                                        cudaStream_t st)
+{
+    if ((long long)T.n > kNoAllocMaxN) return cudaErrorInvalidValue;
+    float *scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess) return e;
+    // k_mass_to_tree overwrites scratch[0, n) before k_find reads it, so
+    // nothing left by an earlier call needs clearing.
+    return launch_find(T, ngroups, ngmax, nbrs, counts, m, scratch, rho, sms, st);
 }
 
 // ---------------------------------------------------------------- density
