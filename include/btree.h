@@ -115,6 +115,39 @@ int btree_build(const float *x, const float *y, const float *z, const float *h,
                 int64_t n, int bucket_size, double alpha, double beta,
                 const bt_allocator *alloc, void *stream, btree_t **out);
 
+/* Per-set parameters of btree_build_batched. */
+#define BT_SET_OCTREE 1 /* b fixed to 2, no Eq. 1 / Eq. 4: the classical octree */
+typedef struct {
+    int bucket_size; /* s >= 1                                  */
+    int flags;       /* 0 or BT_SET_OCTREE                      */
+    double alpha;    /* underfull fraction (Eq. 4), e.g. 0.5    */
+    double beta;     /* empty-cell limit (Eq. 4), e.g. 0.5      */
+} bt_set_params;
+
+/*
+ * btree_build_batched -- BuildTree for many independent particle sets at once
+ * (one set of launches for all of them).
+ *
+ * x, y, z, h : device float32 [offsets[nsets]]: the sets concatenated;
+ *              set i is particles [offsets[i], offsets[i+1]).
+ * offsets    : host int64 [nsets+1], offsets[0] = 0, non-decreasing,
+ *              offsets[nsets] < 2^31.
+ * nsets      : 1 <= nsets <= 2^24.
+ * params     : host [nsets] per-set parameters, or NULL for s = 16,
+ *              alpha = beta = 0.5.
+ * Every set gets its own tree (its root box is its own bounding box); the
+ * result for a set is exactly what btree_build gives for that set alone.
+ * With BT_SET_OCTREE the set is split into octants at every level (the
+ * paper's octree comparison baseline; same neighbour lists).
+ * The find and density calls accept a batched tree: row i of `neighbors` is
+ * the i-th particle of the concatenation, its entries are indices WITHIN the
+ * particle's own set (0 .. set size - 1), ascending.
+ * Errors and synchronisation: as btree_build.
+ */
+int btree_build_batched(const float *x, const float *y, const float *z, const float *h,
+                        const int64_t *offsets, int nsets, const bt_set_params *params,
+                        const bt_allocator *alloc, void *stream, btree_t **out);
+
 /*
  * btree_find_neighbors -- FindNeighbors (Algorithm 2) for every particle.
  *

@@ -15,7 +15,9 @@ Parity status per function (what pins it, see ``tests/test_oracle_pins.py``):
   child_coord/id    -- the worked example of Sec. 3.1 (coords (7,8,1), j=187).
   cell_range        -- the 2D example of Fig. 1 (x cells 2..4, y cells 3..4).
   build             -- ratio loop collapses a clustered cell to b=2 (Sec. 3.1
-                       step 3), invariants (each particle in one leaf, boxes tile).
+                       step 3), invariants (each particle in one leaf, boxes tile);
+                       octree mode: a 8x8x8 lattice at s=1 is the perfect
+                       depth-3 octree (73 internal cells).
   find_brute        -- closed-form lattice counts (92 interior neighbours at
                        h=1.5, strict <), hand-checked tiny sets, pair symmetry.
   find_tree         -- equal to find_brute (the definition) on random sets.
@@ -74,6 +76,8 @@ def _load():
         lib.orc_radius2.argtypes = [ctypes.c_float]
         lib.orc_build.restype = vp
         lib.orc_build.argtypes = [vp, vp, vp, i64, i64, dbl, dbl]
+        lib.orc_build2.restype = vp
+        lib.orc_build2.argtypes = [vp, vp, vp, i64, i64, dbl, dbl, ctypes.c_int]
         lib.orc_free.restype = None
         lib.orc_free.argtypes = [vp]
         for f in ("orc_num_nodes", "orc_num_slots"):
@@ -158,13 +162,13 @@ def num_threads() -> int:
 class OracleTree:
     """The oracle's b-tree (Algorithm 1) over float32 positions."""
 
-    def __init__(self, x, y, z, bucket_size=16, alpha=0.5, beta=0.5):
+    def __init__(self, x, y, z, bucket_size=16, alpha=0.5, beta=0.5, octree=False):
         lib = _load()
         self.x, self.y, self.z = _f32(x), _f32(y), _f32(z)
         self.n = int(self.x.shape[0])
         self.bucket_size = int(bucket_size)
-        self._t = lib.orc_build(_ptr(self.x), _ptr(self.y), _ptr(self.z), self.n,
-                                self.bucket_size, float(alpha), float(beta))
+        self._t = lib.orc_build2(_ptr(self.x), _ptr(self.y), _ptr(self.z), self.n,
+                                 self.bucket_size, float(alpha), float(beta), int(bool(octree)))
         if not self._t:
             raise ValueError("oracle build rejected its arguments")
         self._lib = lib

@@ -153,6 +153,7 @@ typedef struct {
 typedef struct {
     int64_t n, s;
     double alpha, beta;
+    int octree;           /* b fixed to 2 at every split (no Eq. 1 / Eq. 4) */
     const float *x, *y, *z;
     int64_t *perm;        /* original particle indices in tree order */
     orc_node *nodes;
@@ -207,8 +208,8 @@ static void build_node(orc_tree *t, int64_t ni)
         return;
     }
 
-    /* Step 1: branching factor (Eq. 1). */
-    int64_t b = orc_branching_factor(nd.count, t->s);
+    /* Step 1: branching factor (Eq. 1); the octree always halves. */
+    int64_t b = t->octree ? 2 : orc_branching_factor(nd.count, t->s);
     int64_t *counts = NULL;
     const double under = t->alpha * (double)t->s;
     for (;;) {
@@ -311,12 +312,16 @@ static void build_node(orc_tree *t, int64_t ni)
     }
 }
 
-orc_tree *orc_build(const float *x, const float *y, const float *z, int64_t n,
-                    int64_t s, double alpha, double beta)
+/* octree != 0: the classical octree the paper compares with (Sec. 2: b = 2
+ * in every dimension at every level; with b = 2 the ratio test of Eq. 4
+ * never halves, so the same BuildTree steps apply). */
+orc_tree *orc_build2(const float *x, const float *y, const float *z, int64_t n,
+                     int64_t s, double alpha, double beta, int octree)
 {
     if (n < 0 || s < 1)
         return NULL;
     orc_tree *t = (orc_tree *)calloc(1, sizeof(orc_tree));
+    t->octree = octree;
     t->n = n;
     t->s = s;
     t->alpha = alpha;
@@ -355,6 +360,12 @@ orc_tree *orc_build(const float *x, const float *y, const float *z, int64_t n,
     t->scratch_perm = NULL;
     t->cell = NULL;
     return t;
+}
+
+orc_tree *orc_build(const float *x, const float *y, const float *z, int64_t n,
+                    int64_t s, double alpha, double beta)
+{
+    return orc_build2(x, y, z, n, s, alpha, beta, 0);
 }
 
 void orc_free(orc_tree *t)

@@ -17,7 +17,7 @@ import os
 import threading
 
 __all__ = [
-    "BtreeError", "Tree", "btree_build", "btree_find_neighbors",
+    "BtreeError", "Tree", "btree_build", "btree_build_batched", "btree_find_neighbors",
     "btree_find_neighbors_density", "btree_find_neighbors_density_noalloc",
     "btree_noalloc_max_particles", "sph_density", "btree_status", "btree_get_info",
     "btree_export", "btree_free", "btree_strerror", "btree_version", "btree_kernel_launches",
@@ -73,6 +73,9 @@ def _load():
         lib.btree_build.restype = ctypes.c_int
         lib.btree_build.argtypes = [vp, vp, vp, vp, i64, ctypes.c_int, dbl, dbl, vp, vp,
                                     ctypes.POINTER(vp)]
+        lib.btree_build_batched.restype = ctypes.c_int
+        lib.btree_build_batched.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int, vp, vp, vp,
+                                            ctypes.POINTER(vp)]
         lib.btree_find_neighbors.restype = ctypes.c_int
         lib.btree_find_neighbors.argtypes = [vp, ctypes.c_int, vp, vp, vp]
         lib.btree_find_neighbors_density.restype = ctypes.c_int
@@ -167,6 +170,46 @@ def btree_build(x, y, z, h, bucket_size: int = 16, alpha: float = 0.5, beta: flo
     st = lib.btree_build(*ptrs, n, int(bucket_size), float(alpha), float(beta), None,
                          ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(t._ptr))
     _check(st, "btree_build")
+    t.status = st
+    t.n = n
+    return t
+
+
+BT_SET_OCTREE = 1
+
+
+class _SetParams(ctypes.Structure):
+    _fields_ = [("bucket_size", ctypes.c_int), ("flags", ctypes.c_int),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double)]
+
+
+def btree_build_batched(x, y, z, h, offsets, params=None, stream=None,
+                        tree: Tree | None = None) -> Tree:
+    """BuildTree for many sets at once.  x, y, z, h: the sets concatenated;
+    offsets: nsets+1 ints; params: per-set dicts with bucket_size, alpha,
+    beta, octree (or one dict for all, or None for the defaults)."""
+    import torch
+    lib = _load()
+    n = int(x.numel())
+    offs = [int(v) for v in offsets]
+    nsets = len(offs) - 1
+    if nsets < 1 or offs[0] != 0 or offs[-1] != n:
+        raise ValueError("offsets must run from 0 to the number of particles")
+    ptrs = [_dptr(a, torch.float32, nm, n) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (h, "h"))]
+    c_offs = (ctypes.c_int64 * (nsets + 1))(*offs)
+    c_par = None
+    if params is not None:
+        plist = [params] * nsets if isinstance(params, dict) else list(params)
+        c_par = (_SetParams * nsets)()
+        for i, p in enumerate(plist):
+            c_par[i].bucket_size = int(p.get("bucket_size", 16))
+            c_par[i].flags = BT_SET_OCTREE if p.get("octree", False) else 0
+            c_par[i].alpha = float(p.get("alpha", 0.5))
+            c_par[i].beta = float(p.get("beta", 0.5))
+    t = tree if tree is not None else Tree()
+    st = lib.btree_build_batched(*ptrs, c_offs, nsets, c_par, None,
+                                 ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(t._ptr))
+    _check(st, "btree_build_batched")
     t.status = st
     t.n = n
     return t

@@ -48,8 +48,12 @@ struct btree {
     Counters *ctr = nullptr;
     Counters *hctr = nullptr;  // pinned host mirror
     float *smass = nullptr;
-    int *halve_thr = nullptr;   // device [kMaxB+1]
-    int *hhalve_thr = nullptr;  // pinned host copy
+    // per-set tables (device) and their pinned host staging
+    int nsets = 0, cap_sets = 0;
+    int *set_start = nullptr, *set_s = nullptr, *set_na = nullptr, *set_thr = nullptr;
+    int *set_flags = nullptr, *set_flags_in = nullptr, *set_bbox = nullptr;
+    int *h_sets = nullptr;  // [4 * cap_sets + 1]: start[n+1], s[n], na[n], flags[n]
+    int *h_thr = nullptr;   // [cap_sets * (kMaxB + 1)]
 
     int ngroups = 0;
     bt_info info{};
@@ -106,8 +110,11 @@ void free_all(btree *t)
     for (int k = 0; k < 2; k++) { dev_free(t, t->wpos[k]); dev_free(t, t->wh[k]); dev_free(t, t->big_ids[k]); }
     dev_free(t, t->hist); dev_free(t, t->hoff); dev_free(t, t->cursor); dev_free(t, t->tiles);
     dev_free(t, t->big); dev_free(t, t->small); dev_free(t, t->ctr); dev_free(t, t->smass);
-    dev_free(t, t->halve_thr);
-    t->halve_thr = nullptr;
+    dev_free(t, t->set_start); dev_free(t, t->set_s); dev_free(t, t->set_na); dev_free(t, t->set_thr);
+    dev_free(t, t->set_flags); dev_free(t, t->set_flags_in); dev_free(t, t->set_bbox);
+    t->set_start = t->set_s = t->set_na = t->set_thr = nullptr;
+    t->set_flags = t->set_flags_in = t->set_bbox = nullptr;
+    t->cap_sets = 0;
     t->geom = nullptr; t->walk = nullptr; t->slots = nullptr; t->groups = nullptr;
     t->spos = nullptr; t->sh = nullptr; t->inv = nullptr;
     for (int k = 0; k < 2; k++) { t->wpos[k] = nullptr; t->wh[k] = nullptr; t->big_ids[k] = nullptr; }
@@ -121,7 +128,13 @@ TreeDev view(const btree *t)
 {
     TreeDev T;
     T.n = (int)t->n;
-    T.s = t->s;
+    T.nsets = t->nsets;
+    T.set_start = t->set_start;
+    T.set_s = t->set_s;
+    T.set_na = t->set_na;
+    T.set_thr = t->set_thr;
+    T.set_flags = t->set_flags;
+    T.set_bbox = t->set_bbox;
     T.geom = t->geom;
     T.walk = t->walk;
     T.slots = t->slots;
@@ -130,7 +143,6 @@ TreeDev view(const btree *t)
     T.sh = t->sh;
     T.inv = t->inv;
     T.ctr = t->ctr;
-    T.halve_thr = t->halve_thr;
     T.cap_nodes = t->cap_nodes;
     T.cap_slots = t->cap_slots;
     T.cap_groups = t->cap_groups;
@@ -152,8 +164,9 @@ int ensure_particle_caps(btree *t, int64_t n)
         t->cap_n = c;
     }
     const int64_t s = t->s;
+    const int64_t ns = std::max(t->nsets, 1);
     int64_t want_groups = nn + 1;
-    int64_t want_small = nn / (s + 1) + 2;
+    int64_t want_small = nn / (s + 1) + 2 + ns;
     int64_t want_big = nn / (kSmallCap + 1) + 2;
     if (t->cap_groups < want_groups) {
         if (!realloc_dev(t, t->groups, 0, want_groups, false)) return BT_ERR_OOM;
@@ -170,7 +183,7 @@ int ensure_particle_caps(btree *t, int64_t n)
             return BT_ERR_OOM;
         t->cap_big = (int)want_big;
     }
-    int64_t want_nodes = std::min<int64_t>(INT32_MAX / 2, 3 * nn / (s + 1) + 1024);
+    int64_t want_nodes = std::min<int64_t>(INT32_MAX / 2, 3 * nn / (s + 1) + 1024 + ns);
     if (t->cap_nodes < want_nodes) {
         if (!realloc_dev(t, t->geom, 0, want_nodes, false) || !realloc_dev(t, t->walk, 0, want_nodes, false))
             return BT_ERR_OOM;
@@ -184,10 +197,6 @@ int ensure_particle_caps(btree *t, int64_t n)
     if (!t->ctr) {
         t->ctr = static_cast<Counters *>(dev_alloc(t, sizeof(Counters)));
         if (!t->ctr) return BT_ERR_OOM;
-    }
-    if (!t->halve_thr) {
-        t->halve_thr = static_cast<int *>(dev_alloc(t, sizeof(int) * (kMaxB + 1)));
-        if (!t->halve_thr) return BT_ERR_OOM;
     }
     return BT_OK;
 }
@@ -204,6 +213,30 @@ int ensure_hist(btree *t, int64_t need)
     return BT_OK;
 }
 
+// Device tables and pinned staging for nsets particle sets.
+int ensure_set_caps(btree *t, int nsets)
+{
+    if (t->cap_sets >= nsets && t->set_start) return BT_OK;
+    const int c = std::max(nsets, 1);
+    if (!realloc_dev(t, t->set_start, 0, c + 1, false) || !realloc_dev(t, t->set_s, 0, c, false) ||
+        !realloc_dev(t, t->set_na, 0, c, false) ||
+        !realloc_dev(t, t->set_thr, 0, (int64_t)c * (kMaxB + 1), false) ||
+        !realloc_dev(t, t->set_flags, 0, c, false) || !realloc_dev(t, t->set_flags_in, 0, c, false) ||
+        !realloc_dev(t, t->set_bbox, 0, 6 * c, false))
+        return BT_ERR_OOM;
+    if (t->h_sets) cudaFreeHost(t->h_sets);
+    if (t->h_thr) cudaFreeHost(t->h_thr);
+    t->h_sets = nullptr;
+    t->h_thr = nullptr;
+    if (cudaMallocHost(&t->h_sets, sizeof(int) * (4 * (size_t)c + 1)) != cudaSuccess ||
+        cudaMallocHost(&t->h_thr, sizeof(int) * (size_t)c * (kMaxB + 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return BT_ERR_OOM;
+    }
+    t->cap_sets = c;
+    return BT_OK;
+}
+
 int read_counters(btree *t)
 {
     cudaMemcpyAsync(t->hctr, t->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, t->st);
@@ -214,34 +247,33 @@ int read_counters(btree *t)
 
 constexpr int kRetry = 100;
 
-int do_build(btree *t, const float *x, const float *y, const float *z, const float *h, int na)
+int do_build(btree *t, const float *x, const float *y, const float *z, const float *h)
 {
-    const int n = (int)t->n;
+    const int ns = t->nsets;
     cudaStream_t st = t->st;
     TreeDev T = view(t);
-    // Eq. 4 acceptance bound per b for this beta: halve iff u > beta*b^3 in
-    // binary64, i.e. iff u > floor(beta*b^3) (u is an integer).
-    for (int b = 0; b <= kMaxB; b++) {
-        const double bb = (double)b * (double)b * (double)b;
-        const double thr = t->beta * bb;
-        t->hhalve_thr[b] = thr < 0.0 ? -1 : (thr >= 2147483647.0 ? INT32_MAX : (int)std::floor(thr));
-    }
-    cudaMemcpyAsync(t->halve_thr, t->hhalve_thr, sizeof(int) * (kMaxB + 1), cudaMemcpyHostToDevice, st);
+    // per-set tables (staged on the host by the caller)
+    cudaMemcpyAsync(t->set_start, t->h_sets, sizeof(int) * (ns + 1), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(t->set_s, t->h_sets + (ns + 1), sizeof(int) * ns, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(t->set_na, t->h_sets + (2 * ns + 1), sizeof(int) * ns, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(t->set_flags_in, t->h_sets + (3 * ns + 1), sizeof(int) * ns, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(t->set_thr, t->h_thr, sizeof(int) * (size_t)ns * (kMaxB + 1), cudaMemcpyHostToDevice, st);
     launch_init_counters(t->ctr, st);
+    launch_set_int(&t->ctr->nnodes, ns, st);  // nodes 0..ns-1 are the roots
+    launch_init_sets(T, t->set_flags_in, st);
     cudaEventRecord(t->ev0, st);
-    launch_bbox(x, y, z, h, n, t->ctr, t->sms, st);
-    launch_root(T, n, st);
-    launch_set_small_root(t->small, t->big_ids[0], n, t->s, t->ctr, st);
+    launch_bbox(T, x, y, z, h, t->sms, st);
+    launch_root_sets(T, t->big_ids[0], t->small, st);
+    launch_copy_leaf_roots(T, x, y, z, h, t->sms, st);
     int rc = read_counters(t);
     if (rc != BT_OK) return rc;
     if (t->hctr->status & kStNonfinite) return BT_ERR_NONFINITE;
+    if (t->hctr->status & kStCapSmall) return kRetry;
 
-    if (n > 0 && n <= t->s) {
-        launch_root_leaf(T, x, y, z, h, n, t->sms, st);
-    } else if (n > 0) {
+    {
         Src in{x, y, z, h, nullptr, nullptr};
         Src src = in;
-        int nb = n > kSmallCap ? 1 : 0;
+        int nb = t->hctr->nbig_next;
         int cur = 0, dst = 0;
         int64_t nslots = 0;
         while (nb > 0) {
@@ -262,7 +294,7 @@ int do_build(btree *t, const float *x, const float *y, const float *z, const flo
             for (int it = 0; it < 16; it++) {
                 launch_set_int(&t->ctr->again, 0, st);
                 launch_big_hist(T, t->big, nb, chunks, src, t->hist, t->sms, st);
-                launch_big_ratio(t->big, nb, t->hist, hist_total, na, t->halve_thr, t->ctr, t->sms, st);
+                launch_big_ratio(T, t->big, nb, t->hist, hist_total, t->sms, st);
                 if ((rc = read_counters(t)) != BT_OK) return rc;
                 if (!t->hctr->again) break;
                 launch_big_zero(t->big, nb, t->hist, hist_total, t->sms, st);
@@ -288,7 +320,7 @@ int do_build(btree *t, const float *x, const float *y, const float *z, const flo
         const int nsmall = t->hctr->nsmall;
         Src s0{nullptr, nullptr, nullptr, nullptr, t->wpos[0], t->wh[0]};
         Src s1{nullptr, nullptr, nullptr, nullptr, t->wpos[1], t->wh[1]};
-        launch_small(T, t->small, std::min(nsmall, t->cap_small), s0, s1, in, na, t->beta, t->sms, st);
+        launch_small(T, t->small, std::min(nsmall, t->cap_small), s0, s1, in, t->sms, st);
     }
     cudaEventRecord(t->ev1, st);
     if ((rc = read_counters(t)) != BT_OK) return rc;
@@ -317,6 +349,94 @@ bool is_finite_d(double v) { return std::isfinite(v); }
 
 }  // namespace
 
+// Shared front end of btree_build and btree_build_batched: the per-set
+// tables must already be staged in t->h_sets / t->h_thr.
+static int build_core(btree *t, const float *x, const float *y, const float *z, const float *h)
+{
+    int rc = BT_OK;
+    for (int attempt = 0; attempt < 6; attempt++) {
+        rc = ensure_particle_caps(t, t->n);
+        if (rc != BT_OK) break;
+        rc = do_build(t, x, y, z, h);
+        if (rc != kRetry) break;
+        // grow the tree-size buffers and build again
+        int64_t cn = std::min<int64_t>((int64_t)t->cap_nodes * 2, INT32_MAX / 2);
+        int64_t cs = std::min<int64_t>((int64_t)t->cap_slots * 2, INT32_MAX / 2);
+        int64_t cm = std::min<int64_t>((int64_t)t->cap_small * 2 + 1024, INT32_MAX / 2);
+        if (!realloc_dev(t, t->geom, 0, cn, false) || !realloc_dev(t, t->walk, 0, cn, false) ||
+            !realloc_dev(t, t->slots, 0, cs, false) || !realloc_dev(t, t->small, 0, cm, false)) {
+            rc = BT_ERR_OOM;
+            break;
+        }
+        t->cap_nodes = (int)cn;
+        t->cap_slots = (int)cs;
+        t->cap_small = (int)cm;
+        rc = BT_ERR_CAPACITY;
+    }
+    return rc;
+}
+
+// Creates or re-targets the handle (allocator, stream); nullptr on failure.
+static btree *prepare_handle(btree_t **out, const bt_allocator *alloc, void *stream, int *rc)
+{
+    std::call_once(g_attr_once, [] {
+        g_attr_err = build_init_attributes();
+        if (g_attr_err == cudaSuccess) g_attr_err = find_init_attributes();
+    });
+    if (g_attr_err != cudaSuccess) {
+        *rc = to_status(g_attr_err);
+        return nullptr;
+    }
+    btree *t = *out;
+    bool fresh = false;
+    if (!t) {
+        t = new (std::nothrow) btree();
+        if (!t) {
+            *rc = BT_ERR_OOM;
+            return nullptr;
+        }
+        fresh = true;
+        cudaGetDevice(&t->device);
+        cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, t->device);
+        if (cudaMallocHost(&t->hctr, sizeof(Counters)) != cudaSuccess ||
+            cudaEventCreate(&t->ev0) != cudaSuccess || cudaEventCreate(&t->ev1) != cudaSuccess) {
+            cudaGetLastError();
+            delete t;
+            *rc = BT_ERR_CUDA;
+            return nullptr;
+        }
+        *out = t;
+    }
+    if (alloc) {
+        if (!fresh && !t->has_al) free_all(t);  // buffers came from another allocator
+        t->al = *alloc;
+        t->has_al = true;
+    } else if (t->has_al) {
+        free_all(t);
+        t->has_al = false;
+    }
+    t->st = static_cast<cudaStream_t>(stream);
+    *rc = BT_OK;
+    return t;
+}
+
+// Eq. 4 integer bounds of one set: n_j <= alpha*s in binary64 is n_j <= na;
+// halving iff u > beta*b^3 in binary64 is u > thr[b] (u, n_j integers).
+static void stage_set(btree *t, int i, int ns, int s, double alpha, double beta, int flags)
+{
+    const double under = alpha * (double)s;
+    const int na = under < 0.0 ? -1 : (under >= 2147483647.0 ? INT32_MAX : (int)std::floor(under));
+    t->h_sets[(ns + 1) + i] = s;
+    t->h_sets[(2 * ns + 1) + i] = na;
+    t->h_sets[(3 * ns + 1) + i] = flags;
+    int *thr = t->h_thr + (size_t)i * (kMaxB + 1);
+    for (int b = 0; b <= kMaxB; b++) {
+        const double bb = (double)b * (double)b * (double)b;
+        const double v = beta * bb;
+        thr[b] = v < 0.0 ? -1 : (v >= 2147483647.0 ? INT32_MAX : (int)std::floor(v));
+    }
+}
+
 extern "C" {
 
 int btree_build(const float *x, const float *y, const float *z, const float *h, int64_t n,
@@ -328,65 +448,58 @@ int btree_build(const float *x, const float *y, const float *z, const float *h, 
         return BT_ERR_ARG;
     if (n > 0 && (!x || !y || !z || !h)) return BT_ERR_ARG;
     if (alloc && (!alloc->alloc || !alloc->free)) return BT_ERR_ARG;
-    std::call_once(g_attr_once, [] {
-        g_attr_err = build_init_attributes();
-        if (g_attr_err == cudaSuccess) g_attr_err = find_init_attributes();
-    });
-    if (g_attr_err != cudaSuccess) return to_status(g_attr_err);
-
-    btree *t = *out;
-    bool fresh = false;
-    if (!t) {
-        t = new (std::nothrow) btree();
-        if (!t) return BT_ERR_OOM;
-        fresh = true;
-        cudaGetDevice(&t->device);
-        cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, t->device);
-        if (cudaMallocHost(&t->hctr, sizeof(Counters)) != cudaSuccess ||
-            cudaMallocHost(&t->hhalve_thr, sizeof(int) * (kMaxB + 1)) != cudaSuccess ||
-            cudaEventCreate(&t->ev0) != cudaSuccess || cudaEventCreate(&t->ev1) != cudaSuccess) {
-            cudaGetLastError();
-            delete t;
-            return BT_ERR_CUDA;
-        }
-    }
-    if (alloc) {
-        if (!fresh && !t->has_al) free_all(t);  // buffers came from another allocator
-        t->al = *alloc;
-        t->has_al = true;
-    } else if (t->has_al) {
-        free_all(t);
-        t->has_al = false;
-    }
-    t->st = static_cast<cudaStream_t>(stream);
+    int rc;
+    btree *t = prepare_handle(out, alloc, stream, &rc);
+    if (!t) return rc;
     t->n = n;
     t->s = bucket_size;
     t->alpha = alpha;
     t->beta = beta;
-    // n_j <= alpha*s in binary64, as an integer bound on n_j
-    const double under = alpha * (double)bucket_size;
-    int na = under < 0.0 ? -1 : (under >= 2147483647.0 ? INT32_MAX : (int)std::floor(under));
+    t->nsets = 1;
+    if ((rc = ensure_set_caps(t, 1)) != BT_OK) return rc;
+    t->h_sets[0] = 0;
+    t->h_sets[1] = (int)n;
+    stage_set(t, 0, 1, bucket_size, alpha, beta, 0);
+    return build_core(t, x, y, z, h);
+}
 
-    int rc = BT_OK;
-    for (int attempt = 0; attempt < 6; attempt++) {
-        rc = ensure_particle_caps(t, n);
-        if (rc != BT_OK) break;
-        rc = do_build(t, x, y, z, h, na);
-        if (rc != kRetry) break;
-        // grow the tree-size buffers and build again
-        int64_t cn = std::min<int64_t>((int64_t)t->cap_nodes * 2, INT32_MAX / 2);
-        int64_t cs = std::min<int64_t>((int64_t)t->cap_slots * 2, INT32_MAX / 2);
-        if (!realloc_dev(t, t->geom, 0, cn, false) || !realloc_dev(t, t->walk, 0, cn, false) ||
-            !realloc_dev(t, t->slots, 0, cs, false)) {
-            rc = BT_ERR_OOM;
-            break;
-        }
-        t->cap_nodes = (int)cn;
-        t->cap_slots = (int)cs;
-        rc = BT_ERR_CAPACITY;
+int btree_build_batched(const float *x, const float *y, const float *z, const float *h,
+                        const int64_t *offsets, int nsets, const bt_set_params *params,
+                        const bt_allocator *alloc, void *stream, btree_t **out)
+{
+    if (!out || !offsets || nsets < 1 || nsets > (1 << 24)) return BT_ERR_ARG;
+    if (offsets[0] != 0) return BT_ERR_ARG;
+    for (int i = 0; i < nsets; i++)
+        if (offsets[i + 1] < offsets[i]) return BT_ERR_ARG;
+    const int64_t n = offsets[nsets];
+    if (n >= (int64_t)INT32_MAX) return BT_ERR_ARG;
+    if (n > 0 && (!x || !y || !z || !h)) return BT_ERR_ARG;
+    if (alloc && (!alloc->alloc || !alloc->free)) return BT_ERR_ARG;
+    int smin = 1 << 20;
+    for (int i = 0; i < nsets; i++) {
+        const int s = params ? params[i].bucket_size : 16;
+        const double a = params ? params[i].alpha : 0.5, b = params ? params[i].beta : 0.5;
+        if (s < 1 || s > (1 << 20) || !is_finite_d(a) || !is_finite_d(b)) return BT_ERR_ARG;
+        if (params && (params[i].flags & ~BT_SET_OCTREE)) return BT_ERR_ARG;
+        smin = std::min(smin, s);
     }
-    *out = t;
-    return rc;
+    int rc;
+    btree *t = prepare_handle(out, alloc, stream, &rc);
+    if (!t) return rc;
+    t->n = n;
+    t->s = smin;
+    t->alpha = params ? params[0].alpha : 0.5;
+    t->beta = params ? params[0].beta : 0.5;
+    t->nsets = nsets;
+    if ((rc = ensure_set_caps(t, nsets)) != BT_OK) return rc;
+    for (int i = 0; i <= nsets; i++) t->h_sets[i] = (int)offsets[i];
+    for (int i = 0; i < nsets; i++) {
+        const int s = params ? params[i].bucket_size : 16;
+        const double a = params ? params[i].alpha : 0.5, b = params ? params[i].beta : 0.5;
+        const int f = params && (params[i].flags & BT_SET_OCTREE) ? kSetOctree : 0;
+        stage_set(t, i, nsets, s, a, b, f);
+    }
+    return build_core(t, x, y, z, h);
 }
 
 int btree_find_neighbors(const btree_t *t, int ngmax, int32_t *neighbors, int32_t *counts, void *stream)
@@ -533,7 +646,8 @@ void btree_free(btree_t *t)
     if (!t) return;
     free_all(t);
     if (t->hctr) cudaFreeHost(t->hctr);
-    if (t->hhalve_thr) cudaFreeHost(t->hhalve_thr);
+    if (t->h_sets) cudaFreeHost(t->h_sets);
+    if (t->h_thr) cudaFreeHost(t->h_thr);
     if (t->ev0) cudaEventDestroy(t->ev0);
     if (t->ev1) cudaEventDestroy(t->ev1);
     delete t;

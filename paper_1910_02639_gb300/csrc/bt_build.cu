@@ -1,16 +1,19 @@
-// bt_build.cu -- BuildTree (Algorithm 1 of arXiv:1910.02639) on the GPU.
+// bt_build.cu -- BuildTree (Algorithm 1 of arXiv:1910.02639) on the GPU, for
+// one or many particle sets at once.
 //
 // Level-synchronous for cells with more than kSmallCap particles ("big"
-// cells): one pass per candidate branching factor computes every particle's
-// sub-cell (Eqs. 2-3) and a global histogram n_j; one block per cell applies
-// the ratio test (Eq. 4) and halves b when it fails; an exclusive scan of the
+// cells), over all sets together: one pass per candidate branching factor
+// computes every particle's sub-cell (Eqs. 2-3) and a global histogram n_j;
+// the ratio test (Eq. 4) accepts b or halves it; an exclusive scan of the
 // accepted histograms places the sub-cells; a scatter moves each particle to
 // its sub-cell.  Cells of at most kSmallCap particles are built to the bottom
 // by one warp each, entirely in shared memory (depth-first, explicit stack).
 //
 // Particle records are float4 (x, y, z, original index as int bits) plus a
 // float h, in "tree order" once final: the particles of every cell, and so of
-// every sub-tree, occupy one contiguous range, sub-cells in id order.
+// every sub-tree, occupy one contiguous range, sub-cells in id order.  Each
+// set's particles stay inside that set's input range; node i < nsets is the
+// root of set i.
 #include "bt_internal.cuh"
 #include "bt_build.cuh"
 
@@ -18,23 +21,33 @@
 
 namespace bt {
 
-// ------------------------------------------------------------------ bbox
-__global__ void __launch_bounds__(256) k_bbox(const float *__restrict__ x,
-                                              const float *__restrict__ y,
-                                              const float *__restrict__ z,
-                                              const float *__restrict__ h, int n,
-                                              Counters *ctr)
+__device__ __forceinline__ void emit_groups(const TreeDev &T, int set, int start, int cnt)
 {
-    float mn0 = FLT_MAX, mn1 = FLT_MAX, mn2 = FLT_MAX;
-    float mx0 = -FLT_MAX, mx1 = -FLT_MAX, mx2 = -FLT_MAX;
-    bool bad = false;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        float a = x[i], b = y[i], c = z[i], hh = h[i];
-        bad |= !isfinite(a) || !isfinite(b) || !isfinite(c) || !isfinite(hh) || !(hh >= 0.0f);
-        mn0 = fminf(mn0, a); mx0 = fmaxf(mx0, a);
-        mn1 = fminf(mn1, b); mx1 = fmaxf(mx1, b);
-        mn2 = fminf(mn2, c); mx2 = fmaxf(mx2, c);
-    }
+    const int ng = (cnt + kGroupMax - 1) / kGroupMax;
+    const int g0 = atomicAdd(&T.ctr->ngroups, ng);
+    for (int q = 0; q < ng; q++)
+        if (g0 + q < T.cap_groups)
+            T.groups[g0 + q] = make_int2(start + q * kGroupMax,
+                                         group_pack(set, min(kGroupMax, cnt - q * kGroupMax)));
+    if (g0 + ng > T.cap_groups) atomicOr(&T.ctr->status, kStCapGroups);
+}
+
+__device__ __forceinline__ int set_b0(const TreeDev &T, int set, int count)
+{
+    if (T.set_flags[set] & kSetOctree) return 2;
+    return branching_factor(count, T.set_s[set]);
+}
+
+// ------------------------------------------------------------------ bbox
+// Per-set bounding boxes (Eq. 2 "bounds of the domain"), plus a check that
+// every coordinate and h is finite and h >= 0.  A warp whose 32 particles
+// belong to one set keeps running per-lane extrema for that set and reduces
+// them only when its set changes (so a single set costs one flush per warp);
+// a warp that straddles a set boundary updates per lane.
+__device__ __forceinline__ void bbox_flush(int set, float mn0, float mn1, float mn2, float mx0,
+                                           float mx1, float mx2, int *set_bbox)
+{
+    if (set < 0) return;  // warp-uniform
     for (int o = 16; o > 0; o >>= 1) {
         mn0 = fminf(mn0, __shfl_xor_sync(~0u, mn0, o));
         mn1 = fminf(mn1, __shfl_xor_sync(~0u, mn1, o));
@@ -43,56 +56,127 @@ __global__ void __launch_bounds__(256) k_bbox(const float *__restrict__ x,
         mx1 = fmaxf(mx1, __shfl_xor_sync(~0u, mx1, o));
         mx2 = fmaxf(mx2, __shfl_xor_sync(~0u, mx2, o));
     }
-    bad = __any_sync(~0u, bad);
     if ((threadIdx.x & 31) == 0) {
-        atomicMin(&ctr->bbox[0], float_to_ordered(mn0));
-        atomicMin(&ctr->bbox[1], float_to_ordered(mn1));
-        atomicMin(&ctr->bbox[2], float_to_ordered(mn2));
-        atomicMax(&ctr->bbox[3], float_to_ordered(mx0));
-        atomicMax(&ctr->bbox[4], float_to_ordered(mx1));
-        atomicMax(&ctr->bbox[5], float_to_ordered(mx2));
-        if (bad) atomicOr(&ctr->status, kStNonfinite);
+        int *bb = set_bbox + 6 * set;
+        atomicMin(&bb[0], float_to_ordered(mn0));
+        atomicMin(&bb[1], float_to_ordered(mn1));
+        atomicMin(&bb[2], float_to_ordered(mn2));
+        atomicMax(&bb[3], float_to_ordered(mx0));
+        atomicMax(&bb[4], float_to_ordered(mx1));
+        atomicMax(&bb[5], float_to_ordered(mx2));
     }
 }
 
-// Root node from the bounding box (one thread).
-__global__ void k_root(TreeDev T, int n)
+__global__ void __launch_bounds__(256) k_bbox(const float *__restrict__ x,
+                                              const float *__restrict__ y,
+                                              const float *__restrict__ z,
+                                              const float *__restrict__ h, int n,
+                                              const int *set_start, int nsets, int *set_bbox,
+                                              Counters *ctr)
 {
-    Counters *ctr = T.ctr;
+    const int stride = gridDim.x * blockDim.x;
+    const int n_round = (n + 31) & ~31;  // whole warps iterate together
+    int cur = -1;
+    float mn0 = FLT_MAX, mn1 = FLT_MAX, mn2 = FLT_MAX;
+    float mx0 = -FLT_MAX, mx1 = -FLT_MAX, mx2 = -FLT_MAX;
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
+        const bool v = i < n;
+        float a = 0.f, b = 0.f, c = 0.f, hh = 0.f;
+        int set = -1;
+        if (v) {
+            a = x[i]; b = y[i]; c = z[i]; hh = h[i];
+            set = nsets == 1 ? 0 : find_set(set_start, nsets, i);
+            bad |= !isfinite(a) || !isfinite(b) || !isfinite(c) || !isfinite(hh) || !(hh >= 0.0f);
+        }
+        const unsigned same = __match_any_sync(~0u, set);
+        if (same == 0xffffffffu) {
+            if (set != cur) {
+                bbox_flush(cur, mn0, mn1, mn2, mx0, mx1, mx2, set_bbox);
+                cur = set;
+                mn0 = mn1 = mn2 = FLT_MAX;
+                mx0 = mx1 = mx2 = -FLT_MAX;
+            }
+            mn0 = fminf(mn0, a); mn1 = fminf(mn1, b); mn2 = fminf(mn2, c);
+            mx0 = fmaxf(mx0, a); mx1 = fmaxf(mx1, b); mx2 = fmaxf(mx2, c);
+        } else if (set >= 0) {
+            int *bb = set_bbox + 6 * set;
+            atomicMin(&bb[0], float_to_ordered(a));
+            atomicMin(&bb[1], float_to_ordered(b));
+            atomicMin(&bb[2], float_to_ordered(c));
+            atomicMax(&bb[3], float_to_ordered(a));
+            atomicMax(&bb[4], float_to_ordered(b));
+            atomicMax(&bb[5], float_to_ordered(c));
+        }
+    }
+    bbox_flush(cur, mn0, mn1, mn2, mx0, mx1, mx2, set_bbox);
+    if (__any_sync(~0u, bad) && (threadIdx.x & 31) == 0) atomicOr(&ctr->status, kStNonfinite);
+}
+
+__global__ void k_init_sets(int *set_bbox, int *set_flags, const int *flags_in, int nsets)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsets; s += gridDim.x * blockDim.x) {
+        for (int l = 0; l < 3; l++) {
+            set_bbox[6 * s + l] = INT_MAX;
+            set_bbox[6 * s + 3 + l] = INT_MIN;
+        }
+        set_flags[s] = flags_in[s];
+    }
+}
+
+// Roots from the boxes, one thread per set: a set of <= s particles is one
+// leaf (work units now, particles copied by k_copy_leaf_roots), a set of
+// <= kSmallCap particles goes to the warp builder, a larger one to the big
+// levels.
+__device__ void root_set(TreeDev &T, int s, int *big_ids, SmallItem *small)
+{
+    const int start = T.set_start[s], n = T.set_start[s + 1] - start;
     NodeGeom g;
     for (int l = 0; l < 3; l++) {
-        double lo = (double)ordered_to_float(ctr->bbox[l]);
-        double hi = (double)ordered_to_float(ctr->bbox[3 + l]);
+        double lo = (double)ordered_to_float(T.set_bbox[6 * s + l]);
+        double hi = (double)ordered_to_float(T.set_bbox[6 * s + 3 + l]);
         if (n == 0) { lo = 0.0; hi = 0.0; }
         g.lo[l] = lo == 0.0 ? 0.0 : lo;  // canonical +0
         g.hi[l] = hi == 0.0 ? 0.0 : hi;
     }
-    g.start = 0;
+    g.start = start;
     g.count = n;
     g.depth = 0;
-    g.pad = 0;
-    T.geom[0] = g;
+    g.set = s;
+    T.geom[s] = g;
     NodeWalk w;
     make_walk(g, 0, 0, w);
     w.b = 0;  // a leaf until split
-    T.walk[0] = w;
-    ctr->nnodes = 1;
+    T.walk[s] = w;
+    if (n == 0) return;
+    if (n <= T.set_s[s]) {
+        T.set_flags[s] |= kSetLeafRoot;
+        emit_groups(T, s, start, n);
+    } else if (n <= kSmallCap) {
+        const int k = atomicAdd(&T.ctr->nsmall, 1);
+        if (k < T.cap_small) small[k] = SmallItem{s, 2};
+        else atomicOr(&T.ctr->status, kStCapSmall);
+    } else {
+        big_ids[atomicAdd(&T.ctr->nbig_next, 1)] = s;
+    }
 }
 
-// Root with n <= s: copy the input to tree order unchanged; one or more groups.
-__global__ void k_root_leaf(TreeDev T, const float *__restrict__ x, const float *__restrict__ y,
-                            const float *__restrict__ z, const float *__restrict__ h, int n)
+__global__ void k_root_sets(TreeDev T, int *big_ids, SmallItem *small)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < T.nsets; s += gridDim.x * blockDim.x)
+        root_set(T, s, big_ids, small);
+}
+
+// Sets that are one leaf: their particles are final where they are.
+__global__ void k_copy_leaf_roots(TreeDev T, const float *__restrict__ x, const float *__restrict__ y,
+                                  const float *__restrict__ z, const float *__restrict__ h)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.n; i += gridDim.x * blockDim.x) {
+        const int s = T.nsets == 1 ? 0 : find_set(T.set_start, T.nsets, i);
+        if (!(T.set_flags[s] & kSetLeafRoot)) continue;
         T.spos[i] = make_float4(x[i], y[i], z[i], __int_as_float(i));
         T.sh[i] = h[i];
         T.inv[i] = i;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        int ng = (n + kGroupMax - 1) / kGroupMax;
-        for (int q = 0; q < ng; q++)
-            T.groups[q] = make_int2(q * kGroupMax, min(kGroupMax, n - q * kGroupMax));
-        T.ctr->ngroups = ng;
     }
 }
 
@@ -103,7 +187,7 @@ __global__ void k_big_setup(TreeDev T, BigCell *big, const int *ids, int nb)
     if (i >= nb) return;
     int node = ids[i];
     const NodeGeom &g = T.geom[node];
-    int b0 = branching_factor(g.count, T.s);
+    int b0 = set_b0(T, g.set, g.count);
     BigCell c;
     c.node = node;
     c.b0 = b0;
@@ -116,7 +200,7 @@ __global__ void k_big_setup(TreeDev T, BigCell *big, const int *ids, int nb)
     c.ne = 0;
     c.lastj = -1;
     c.halved = 0;
-    c.pad = 0;
+    c.set = g.set;
     c.w[0] = c.w[1] = c.w[2] = 0.0;
     big[i] = c;
 }
@@ -183,7 +267,7 @@ __device__ __forceinline__ int find_cell_by_hist(const BigCell *big, int nb, int
 
 // Per-block walk parameters of the block's cell for its current b.
 __device__ __forceinline__ void block_cell_params(const TreeDev &T, const BigCell &c,
-                                                  NodeGeom &g, NodeWalk &w, bool &ok)
+                                                  NodeGeom &g, NodeWalk &w)
 {
     __shared__ NodeGeom s_g;
     __shared__ NodeWalk s_w;
@@ -195,7 +279,6 @@ __device__ __forceinline__ void block_cell_params(const TreeDev &T, const BigCel
     __syncthreads();
     g = s_g;
     w = s_w;
-    ok = true;
 }
 
 __device__ __forceinline__ int sub_cell_id(const float4 &p, const NodeWalk &w, const NodeGeom &g, int b)
@@ -217,8 +300,7 @@ __global__ void __launch_bounds__(256) k_big_hist(TreeDev T, const BigCell *big,
         if (c.state != 0) continue;  // uniform across the block
         NodeGeom g;
         NodeWalk w;
-        bool ok;
-        block_cell_params(T, c, g, w, ok);
+        block_cell_params(T, c, g, w);
         int p0 = g.start + (chunk - c.chunk_base) * kBigChunk;
         int p1 = min(p0 + kBigChunk, g.start + g.count);
         int *hc = hist + c.hist_base;
@@ -231,8 +313,8 @@ __global__ void __launch_bounds__(256) k_big_hist(TreeDev T, const BigCell *big,
 
 // Per-cell statistics of the current histogram (Eq. 4 numerator, non-empty
 // sub-cells), accumulated over the whole level by all blocks.
-__global__ void __launch_bounds__(256) k_big_count(BigCell *big, int nb, const int *hist, int total,
-                                                   int na)
+__global__ void __launch_bounds__(256) k_big_count(TreeDev T, BigCell *big, int nb, const int *hist,
+                                                   int total)
 {
     for (int e0 = blockIdx.x * blockDim.x; e0 < total; e0 += gridDim.x * blockDim.x) {
         const int e = e0 + threadIdx.x;
@@ -243,7 +325,7 @@ __global__ void __launch_bounds__(256) k_big_count(BigCell *big, int nb, const i
             const int j = e - c.hist_base;
             if (c.state == 0 && j < c.b * c.b * c.b) {
                 const int v = hist[e];
-                u = v <= na;
+                u = v <= T.set_na[c.set];
                 ne = v > 0;
                 lj = v > 0 ? j : -1;
             } else {
@@ -274,20 +356,20 @@ __global__ void __launch_bounds__(256) k_big_count(BigCell *big, int nb, const i
 }
 
 // Ratio test (Eq. 4), one thread per big cell: accept b or halve it.
-__global__ void k_big_decide(BigCell *big, int nb, const int *halve_thr, Counters *ctr)
+__global__ void k_big_decide(TreeDev T, BigCell *big, int nb)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
     BigCell &c = big[i];
     c.halved = 0;
     if (c.state != 0) return;
-    if (c.u > halve_thr[c.b] && c.b > 2) {
+    if (c.u > T.set_thr[c.set * (kMaxB + 1) + c.b] && c.b > 2) {
         c.b = max(2, c.b / 2);
         c.halved = 1;
         c.u = 0;
         c.ne = 0;
         c.lastj = -1;
-        ctr->again = 1;
+        T.ctr->again = 1;
     } else {
         c.state = 1;
     }
@@ -332,12 +414,7 @@ __global__ void k_big_finish(TreeDev T, BigCell *big, int nb, int slot_level_bas
         T.walk[c.node] = w;
         atomicAdd(&T.ctr->noversized, 1);
         atomicOr(&T.ctr->status, kStOversized);
-        int ng = (g.count + kGroupMax - 1) / kGroupMax;
-        int g0 = atomicAdd(&T.ctr->ngroups, ng);
-        for (int q = 0; q < ng; q++)
-            if (g0 + q < T.cap_groups)
-                T.groups[g0 + q] = make_int2(g.start + q * kGroupMax, min(kGroupMax, g.count - q * kGroupMax));
-        if (g0 + ng > T.cap_groups) atomicOr(&T.ctr->status, kStCapGroups);
+        emit_groups(T, c.set, g.start, g.count);
         return;
     }
     c.slot0 = slot_level_base + c.hist_base;
@@ -348,7 +425,7 @@ __global__ void k_big_finish(TreeDev T, BigCell *big, int nb, int slot_level_bas
 }
 
 // Emit the sub-cells of every accepted big cell: slots, child nodes, queues,
-// leaf groups; cursor[e] = first tree position of sub-cell e.
+// leaf work units; cursor[e] = first tree position of sub-cell e.
 __global__ void __launch_bounds__(256) k_big_emit(TreeDev T, const BigCell *big, int nb,
                                                   const int *hist, const int *hoff, int *cursor,
                                                   int dst_buf, int *next_big, SmallItem *small)
@@ -362,12 +439,13 @@ __global__ void __launch_bounds__(256) k_big_emit(TreeDev T, const BigCell *big,
         const int j = e - c.hist_base;
         if (j >= b * b * b) continue;
         const NodeGeom &g = T.geom[c.node];
+        const int s = T.set_s[c.set];
         const int cnt = hist[e];
         const int start = g.start + (hoff[e] - hoff[c.hist_base]);
         cursor[e] = start;
         const int depth = g.depth + 1;
         int child = -1;
-        if (cnt > T.s && depth < kDepthMax) {
+        if (cnt > s && depth < kDepthMax) {
             child = atomicAdd(&T.ctr->nnodes, 1);
             if (child >= T.cap_nodes) {
                 atomicOr(&T.ctr->status, kStCapNodes);
@@ -380,7 +458,7 @@ __global__ void __launch_bounds__(256) k_big_emit(TreeDev T, const BigCell *big,
                 cg.start = start;
                 cg.count = cnt;
                 cg.depth = depth;
-                cg.pad = 0;
+                cg.set = c.set;
                 T.geom[child] = cg;
                 if (cnt > kSmallCap) {
                     next_big[atomicAdd(&T.ctr->nbig_next, 1)] = child;
@@ -391,16 +469,11 @@ __global__ void __launch_bounds__(256) k_big_emit(TreeDev T, const BigCell *big,
                 }
             }
         } else if (cnt > 0) {
-            if (cnt > T.s) {
+            if (cnt > s) {
                 atomicAdd(&T.ctr->noversized, 1);
                 atomicOr(&T.ctr->status, kStOversized);
             }
-            int ng = (cnt + kGroupMax - 1) / kGroupMax;
-            int g0 = atomicAdd(&T.ctr->ngroups, ng);
-            for (int q = 0; q < ng; q++)
-                if (g0 + q < T.cap_groups)
-                    T.groups[g0 + q] = make_int2(start + q * kGroupMax, min(kGroupMax, cnt - q * kGroupMax));
-            if (g0 + ng > T.cap_groups) atomicOr(&T.ctr->status, kStCapGroups);
+            emit_groups(T, c.set, start, cnt);
         }
         T.slots[c.slot0 + j] = Slot{start, cnt, child, 0};
     }
@@ -418,8 +491,7 @@ __global__ void __launch_bounds__(256) k_big_scatter(TreeDev T, const BigCell *b
         BigCell c = big[ci];
         NodeGeom g;
         NodeWalk w;
-        bool ok;
-        block_cell_params(T, c, g, w, ok);
+        block_cell_params(T, c, g, w);
         int p0 = g.start + (chunk - c.chunk_base) * kBigChunk;
         int p1 = min(p0 + kBigChunk, g.start + g.count);
         for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
@@ -550,20 +622,10 @@ __device__ __forceinline__ int warp_sum(int v)
     return v;
 }
 
-__device__ __forceinline__ void emit_groups(const TreeDev &T, int start, int cnt)
-{
-    int ng = (cnt + kGroupMax - 1) / kGroupMax;
-    int g0 = atomicAdd(&T.ctr->ngroups, ng);
-    for (int q = 0; q < ng; q++)
-        if (g0 + q < T.cap_groups)
-            T.groups[g0 + q] = make_int2(start + q * kGroupMax, min(kGroupMax, cnt - q * kGroupMax));
-    if (g0 + ng > T.cap_groups) atomicOr(&T.ctr->status, kStCapGroups);
-}
-
 // One warp builds the whole sub-tree of one cell of <= kSmallCap particles.
 __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const SmallItem *items,
                                                             int nitems, Src src0, Src src1,
-                                                            Src srcin, int na, double beta)
+                                                            Src srcin)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmallSmem &S = reinterpret_cast<SmallSmem *>(smem_raw)[threadIdx.x >> 5];
@@ -575,6 +637,11 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
         const SmallItem item = items[it];
         const NodeGeom G = T.geom[item.node];
         const int base = G.start, m0 = G.count;
+        const int set = G.set;
+        const int s_set = T.set_s[set];
+        const int na = T.set_na[set];
+        const int *thr = T.set_thr + set * (kMaxB + 1);
+        const bool octree = (T.set_flags[set] & kSetOctree) != 0;
         const Src &src = item.src == 0 ? src0 : (item.src == 1 ? src1 : srcin);
         for (int k = lane; k < m0; k += 32) {
             float4 r;
@@ -600,8 +667,8 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                 const int a = F.a, m = F.m;
                 NodeGeom g;
                 for (int l = 0; l < 3; l++) { g.lo[l] = F.lo[l]; g.hi[l] = F.hi[l]; }
-                g.start = base + a; g.count = m; g.depth = F.depth; g.pad = 0;
-                int b = branching_factor(m, T.s);
+                g.start = base + a; g.count = m; g.depth = F.depth; g.set = set;
+                int b = octree ? 2 : branching_factor(m, s_set);
                 for (;;) {
                     if (lane == 0) make_walk(g, b, 0, S.w);
                     __syncwarp();
@@ -618,7 +685,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                     int u = 0;
                     for (int j = lane; j < ncell; j += 32) u += S.hist[j] <= na;
                     u = warp_sum(u);
-                    if (u > T.halve_thr[b] && b > 2) {
+                    if (u > thr[b] && b > 2) {
                         b = max(2, b / 2);
                         __syncwarp();
                         continue;
@@ -654,7 +721,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                         T.walk[F.node] = w;
                         atomicAdd(&T.ctr->noversized, 1);
                         atomicOr(&T.ctr->status, kStOversized);
-                        if (F.emit || F.eself) emit_groups(T, base + a, m);
+                        if (F.emit || F.eself) emit_groups(T, set, base + a, m);
                     }
                     sp--;
                     __syncwarp();
@@ -676,13 +743,13 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                     }
                 }
                 __syncwarp();
-                // a cell of <= kWholeMax particles becomes two work units, split
-                // at the sub-cell boundary nearest its middle (contiguous, and
-                // compact: sub-cell ids run x fastest, so low ids are low z)
+                // a cell of <= kWholeMax particles becomes work units of its own
                 if (F.eself && lane == 0) {
                     if (m <= kGroupMax) {
-                        emit_groups(T, base + a, m);
+                        emit_groups(T, set, base + a, m);
                     } else {
+                        // two units split at the sub-cell boundary nearest the
+                        // middle (sub-cell ids run x fastest: low ids are low z)
                         int bnd = 0, best = m;
                         for (int j = 0; j <= ncell; j++) {
                             const int o = j < ncell ? S.off[j] : m;
@@ -690,10 +757,10 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                             if (d < best) { best = d; bnd = o; }
                         }
                         if (bnd == 0 || bnd == m) {
-                            emit_groups(T, base + a, m);
+                            emit_groups(T, set, base + a, m);
                         } else {
-                            emit_groups(T, base + a, bnd);
-                            emit_groups(T, base + a + bnd, m - bnd);
+                            emit_groups(T, set, base + a, bnd);
+                            emit_groups(T, set, base + a + bnd, m - bnd);
                         }
                     }
                 }
@@ -716,7 +783,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                     const int start = base + a + S.off[j];
                     const int depth = F.depth + 1;
                     int child = -1;
-                    if (cnt > T.s && depth < kDepthMax) {
+                    if (cnt > s_set && depth < kDepthMax) {
                         child = atomicAdd(&T.ctr->nnodes, 1);
                         if (child >= T.cap_nodes) {
                             atomicOr(&T.ctr->status, kStCapNodes);
@@ -726,15 +793,15 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                             int cc[3] = {j % b, (j / b) % b, j / (b * b)};
                             for (int l = 0; l < 3; l++)
                                 child_bounds_w(g.lo[l], g.hi[l], F.w[l], b, cc[l], cg.lo[l], cg.hi[l]);
-                            cg.start = start; cg.count = cnt; cg.depth = depth; cg.pad = 0;
+                            cg.start = start; cg.count = cnt; cg.depth = depth; cg.set = set;
                             T.geom[child] = cg;
                         }
                     } else if (cnt > 0) {
-                        if (cnt > T.s) {
+                        if (cnt > s_set) {
                             atomicAdd(&T.ctr->noversized, 1);
                             atomicOr(&T.ctr->status, kStOversized);
                         }
-                        if (F.emit) emit_groups(T, start, cnt);
+                        if (F.emit) emit_groups(T, set, start, cnt);
                     }
                     T.slots[slot0 + j] = Slot{start, cnt, child, 0};
                 }
@@ -817,24 +884,31 @@ static inline int grid_for(long long work, int per_block, int max_blocks)
     return (int)g;
 }
 
-void launch_bbox(const float *x, const float *y, const float *z, const float *h, int n,
-                 Counters *ctr, int sms, cudaStream_t st)
+void launch_init_sets(const TreeDev &T, const int *flags_in, cudaStream_t st)
 {
     note_launch();
-    k_bbox<<<grid_for(n, 256 * 8, sms * 8), 256, 0, st>>>(x, y, z, h, n, ctr);
+    k_init_sets<<<grid_for(T.nsets, 256, 1 << 16), 256, 0, st>>>(T.set_bbox, T.set_flags, flags_in, T.nsets);
 }
 
-void launch_root(const TreeDev &T, int n, cudaStream_t st)
+void launch_bbox(const TreeDev &T, const float *x, const float *y, const float *z, const float *h,
+                 int sms, cudaStream_t st)
 {
     note_launch();
-    k_root<<<1, 1, 0, st>>>(T, n);
+    k_bbox<<<grid_for(T.n, 256 * 8, sms * 8), 256, 0, st>>>(x, y, z, h, T.n, T.set_start, T.nsets,
+                                                             T.set_bbox, T.ctr);
 }
 
-void launch_root_leaf(const TreeDev &T, const float *x, const float *y, const float *z,
-                      const float *h, int n, int sms, cudaStream_t st)
+void launch_root_sets(const TreeDev &T, int *big_ids, SmallItem *small, cudaStream_t st)
 {
     note_launch();
-    k_root_leaf<<<grid_for(n, 256, sms * 4), 256, 0, st>>>(T, x, y, z, h, n);
+    k_root_sets<<<grid_for(T.nsets, 128, 1 << 16), 128, 0, st>>>(T, big_ids, small);
+}
+
+void launch_copy_leaf_roots(const TreeDev &T, const float *x, const float *y, const float *z,
+                            const float *h, int sms, cudaStream_t st)
+{
+    note_launch();
+    k_copy_leaf_roots<<<grid_for(T.n, 256, sms * 8), 256, 0, st>>>(T, x, y, z, h);
 }
 
 void launch_big_setup(const TreeDev &T, BigCell *big, const int *ids, int nb, cudaStream_t st)
@@ -852,13 +926,13 @@ void launch_big_hist(const TreeDev &T, const BigCell *big, int nb, int chunks, S
     k_big_hist<<<grid_for(chunks, 1, sms * 8), 256, 0, st>>>(T, big, nb, src, hist);
 }
 
-void launch_big_ratio(BigCell *big, int nb, const int *hist, int hist_total, int na,
-                      const int *halve_thr, Counters *ctr, int sms, cudaStream_t st)
+void launch_big_ratio(const TreeDev &T, BigCell *big, int nb, const int *hist, int hist_total, int sms,
+                      cudaStream_t st)
 {
     note_launch();
-    k_big_count<<<grid_for(hist_total, 256, sms * 8), 256, 0, st>>>(big, nb, hist, hist_total, na);
+    k_big_count<<<grid_for(hist_total, 256, sms * 8), 256, 0, st>>>(T, big, nb, hist, hist_total);
     note_launch();
-    k_big_decide<<<grid_for(nb, 128, 1 << 20), 128, 0, st>>>(big, nb, halve_thr, ctr);
+    k_big_decide<<<grid_for(nb, 128, 1 << 20), 128, 0, st>>>(T, big, nb);
 }
 
 void launch_big_zero(const BigCell *big, int nb, int *hist, int hist_total, int sms, cudaStream_t st)
@@ -905,13 +979,12 @@ void launch_big_scatter(const TreeDev &T, const BigCell *big, int nb, int chunks
 }
 
 void launch_small(const TreeDev &T, const SmallItem *items, int nitems, Src src0, Src src1,
-                  Src srcin, int na, double beta, int sms, cudaStream_t st)
+                  Src srcin, int sms, cudaStream_t st)
 {
     if (nitems <= 0) return;
     int blocks = grid_for(nitems, kSmallWarps, sms * 4);
     note_launch();
-    k_small<<<blocks, 32 * kSmallWarps, small_smem_bytes(), st>>>(T, items, nitems, src0, src1,
-                                                                   srcin, na, beta);
+    k_small<<<blocks, 32 * kSmallWarps, small_smem_bytes(), st>>>(T, items, nitems, src0, src1, srcin);
 }
 
 cudaError_t build_init_attributes()
@@ -923,42 +996,21 @@ cudaError_t build_init_attributes()
 __global__ void k_init_counters(Counters *ctr)
 {
     Counters c = {};
-    for (int l = 0; l < 3; l++) {
-        c.bbox[l] = INT_MAX;
-        c.bbox[3 + l] = INT_MIN;
-    }
     *ctr = c;
 }
 
 __global__ void k_set_int(int *p, int v) { *p = v; }
-
-// Queue the root for the warp builder (s < n <= kSmallCap) or the big-cell
-// levels (n > kSmallCap).
-__global__ void k_set_small_root(SmallItem *small, int *big_ids, int n, int s, Counters *ctr)
-{
-    if (n > s && n <= kSmallCap) {
-        small[0] = SmallItem{0, 2};
-        ctr->nsmall = 1;
-    } else if (n > kSmallCap) {
-        big_ids[0] = 0;
-    }
-}
 
 void launch_init_counters(Counters *ctr, cudaStream_t st)
 {
     note_launch();
     k_init_counters<<<1, 1, 0, st>>>(ctr);
 }
+
 void launch_set_int(int *p, int v, cudaStream_t st)
 {
     note_launch();
     k_set_int<<<1, 1, 0, st>>>(p, v);
-}
-void launch_set_small_root(SmallItem *small, int *big_ids, int n, int s, Counters *ctr,
-                           cudaStream_t st)
-{
-    note_launch();
-    k_set_small_root<<<1, 1, 0, st>>>(small, big_ids, n, s, ctr);
 }
 
 }  // namespace bt

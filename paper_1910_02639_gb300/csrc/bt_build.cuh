@@ -4,16 +4,17 @@
 
 namespace bt {
 
-void launch_bbox(const float *x, const float *y, const float *z, const float *h, int n,
-                 Counters *ctr, int sms, cudaStream_t st);
-void launch_root(const TreeDev &T, int n, cudaStream_t st);
-void launch_root_leaf(const TreeDev &T, const float *x, const float *y, const float *z,
-                      const float *h, int n, int sms, cudaStream_t st);
+void launch_init_sets(const TreeDev &T, const int *flags_in, cudaStream_t st);
+void launch_bbox(const TreeDev &T, const float *x, const float *y, const float *z, const float *h,
+                 int sms, cudaStream_t st);
+void launch_root_sets(const TreeDev &T, int *big_ids, SmallItem *small, cudaStream_t st);
+void launch_copy_leaf_roots(const TreeDev &T, const float *x, const float *y, const float *z,
+                            const float *h, int sms, cudaStream_t st);
 void launch_big_setup(const TreeDev &T, BigCell *big, const int *ids, int nb, cudaStream_t st);
 void launch_big_hist(const TreeDev &T, const BigCell *big, int nb, int chunks, Src src, int *hist,
                      int sms, cudaStream_t st);
-void launch_big_ratio(BigCell *big, int nb, const int *hist, int hist_total, int na,
-                      const int *halve_thr, Counters *ctr, int sms, cudaStream_t st);
+void launch_big_ratio(const TreeDev &T, BigCell *big, int nb, const int *hist, int hist_total, int sms,
+                      cudaStream_t st);
 void launch_big_zero(const BigCell *big, int nb, int *hist, int hist_total, int sms, cudaStream_t st);
 void launch_big_finish(const TreeDev &T, BigCell *big, int nb, int slot_level_base, cudaStream_t st);
 void launch_scan(const int *in, int n, int *tile_buf, int *out, cudaStream_t st);
@@ -24,11 +25,9 @@ void launch_big_emit(const TreeDev &T, const BigCell *big, int nb, int hist_tota
 void launch_big_scatter(const TreeDev &T, const BigCell *big, int nb, int chunks, Src src,
                         int *cursor, float4 *dst_pos, float *dst_h, int sms, cudaStream_t st);
 void launch_small(const TreeDev &T, const SmallItem *items, int nitems, Src src0, Src src1,
-                  Src srcin, int na, double beta, int sms, cudaStream_t st);
+                  Src srcin, int sms, cudaStream_t st);
 void launch_init_counters(Counters *ctr, cudaStream_t st);
 void launch_set_int(int *p, int v, cudaStream_t st);
-void launch_set_small_root(SmallItem *small, int *big_ids, int n, int s, Counters *ctr,
-                           cudaStream_t st);
 size_t small_smem_bytes();
 cudaError_t build_init_attributes();
 

@@ -72,6 +72,7 @@ struct FindSmem {
     float box[13];            // PL[3] PH[3] QL[3] QH[3] T
     int njobs, nfront, nnext, ncand, kmin, kmax, range_ovf, ovf_lo, ovf_hi;
     int jfail, cover, gstart, gcount, whi;
+    int gset, set_lo, set_hi;  // the group's particle set and its index range
 };
 
 struct FindArgs {
@@ -137,7 +138,7 @@ __device__ void group_walk(const TreeDev &T, FindSmem &S)
         S.jfail = kJobMax;
         S.ovf_lo = INT_MAX;
         S.ovf_hi = INT_MIN;
-        S.front[0][0] = 0;
+        S.front[0][0] = S.gset;  // root of the group's set
         S.nfront = 1;
         S.nnext = 0;
     }
@@ -496,7 +497,7 @@ __device__ void group_window(const FindArgs &A, FindSmem &S)
             for (int i = i0; i < nb; i += 32) {
                 const uint32_t key = S.key[hl[i]];
                 const int pos = base + b0 + i;
-                if (pos < A.ngmax) row[pos] = kmin + (int)(key >> kSlotBits);
+                if (pos < A.ngmax) row[pos] = kmin - S.set_lo + (int)(key >> kSlotBits);
                 if (DENS) {
                     const int slot = key & (kCap - 1);
                     const float4 Q = S.cand[slot];
@@ -532,7 +533,8 @@ __global__ void __launch_bounds__(kFindThreads, 4) k_find(FindArgs A)
             // ---- queries (warp 0), FP32 only: RN(2h * 2h) is the float
             // rounding of the exact binary64 (2h)^2.
             if (tid < 32) {
-                const int2 grp = T.groups[g];
+                const int2 grp0 = T.groups[g];
+                const int2 grp = make_int2(grp0.x, group_count(grp0.y));
                 const bool v = lane < grp.y;
                 float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
                 float h = 0.0f;
@@ -576,13 +578,18 @@ __global__ void __launch_bounds__(kFindThreads, 4) k_find(FindArgs A)
                     S.box[12] = __fmul_ru(__fmul_ru(rsm, rsm), 1.0f + 0x1p-19f);
                     S.gstart = grp.x;
                     S.gcount = grp.y;
+                    const int gs = group_set(grp0.y);
+                    S.gset = gs;
+                    S.set_lo = T.set_start[gs];
+                    S.set_hi = T.set_start[gs + 1];
                 }
             }
             __syncthreads();
             group_walk(T, S);
 
-            // ---- windows over original index
-            int wlo = 0;
+            // ---- windows over original index (within the set)
+            int wlo = S.set_lo;
+            const int wend = S.set_hi;
             for (;;) {
                 int whi = INT_MAX;
                 if (tid == 0) {
@@ -596,7 +603,7 @@ __global__ void __launch_bounds__(kFindThreads, 4) k_find(FindArgs A)
                 const bool fits = S.ncand <= kCap && (S.ncand == 0 || S.kmax - S.kmin < kSpanMax);
                 if (!fits) {
                     // choose the largest window [wlo, whi) that fits, by histograms
-                    long long span = (long long)T.n - wlo;
+                    long long span = (long long)wend - wlo;
                     if (tid == 0) atomicOr(&T.ctr->status, kStWalk);
                     for (;;) {
                         const int Wd = (int)((span + 255) / 256);
@@ -631,7 +638,7 @@ __global__ void __launch_bounds__(kFindThreads, 4) k_find(FindArgs A)
                     __syncthreads();
                 }
                 group_window<DENS>(A, S);
-                if (whi == INT_MAX || whi >= T.n) break;
+                if (whi == INT_MAX || whi >= wend) break;
                 wlo = whi;
             }
 
@@ -776,9 +783,10 @@ __global__ void __launch_bounds__(256) k_density(TreeDev T, const float *__restr
         const float inv_h = __frcp_rn(h);
         const int c = min(counts[i], ngmax);
         const int32_t *row = nbrs + (long long)i * ngmax;
+        const int off = T.set_start[T.nsets == 1 ? 0 : find_set(T.set_start, T.nsets, i)];
         float acc = 0.0f;
         for (int k = lane; k < c; k += 32) {
-            const int j = row[k];
+            const int j = off + row[k];
             const float4 Q = T.spos[T.inv[j]];
             const float dx = Q.x - P.x, dy = Q.y - P.y, dz = Q.z - P.z;
             const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));

@@ -38,11 +38,12 @@ enum : int {
     kFlagDegen0 = 4,       // zero width in dimension 0 (then 8, 16 for dims 1, 2)
 };
 
-// Exact binary64 box of an internal node plus its particle range (build side).
+// Exact binary64 box of an internal node plus its particle range (build side)
+// and the particle set it belongs to.
 struct __align__(16) NodeGeom {
     double lo[3];
     double hi[3];
-    int start, count, depth, pad;
+    int start, count, depth, set;
 };
 
 // What the walk and the per-particle sub-cell computation read (48 B + range).
@@ -248,7 +249,7 @@ struct BigCell {
     int ne;            // non-empty sub-cells
     int lastj;         // largest non-empty sub-cell id
     int halved;        // b was just halved: histogram to clear
-    int pad;
+    int set;           // particle set of the cell
     double w[3];       // sub-cell widths (hi - lo)/b of the accepted b
 };
 
@@ -257,21 +258,49 @@ struct SmallItem {
     int src;  // 0/1: working buffer holding its particles; 2: the input arrays
 };
 
-// Everything the kernels need to see of one tree.
+// Per-set flags.
+enum : int {
+    kSetOctree = 1,    // b fixed to 2 (no Eq. 1 / Eq. 4): the classical octree
+    kSetLeafRoot = 2,  // the whole set fits one leaf
+};
+
+// Work units are (first tree position, set << 6 | count), count <= 32.
+__device__ __host__ __forceinline__ int group_count(int v) { return v & 63; }
+__device__ __host__ __forceinline__ int group_set(int v) { return v >> 6; }
+__device__ __host__ __forceinline__ int group_pack(int set, int count) { return (set << 6) | count; }
+
+// Everything the kernels need to see of one tree (one or more particle sets;
+// node i < nsets is the root of set i).
 struct TreeDev {
-    int n;
-    int s;
+    int n;               // particles over all sets
+    int nsets;
+    const int *set_start;  // [nsets+1] first particle of each set
+    const int *set_s;      // [nsets] bucket size s
+    const int *set_na;     // [nsets] largest n_j counted as underfull (alpha s, Eq. 4)
+    const int *set_thr;    // [nsets][kMaxB+1]: accept b iff u <= thr (beta b^3, Eq. 4)
+    int *set_flags;        // [nsets]
+    int *set_bbox;         // [nsets][6] ordered-int min x,y,z, max x,y,z
     NodeGeom *geom;
     NodeWalk *walk;
     Slot *slots;
     int2 *groups;
-    const int *halve_thr;  // [kMaxB+1]: accept b iff u <= halve_thr[b]
     float4 *spos;   // tree order: x, y, z, orig index (bits)
     float *sh;      // tree order: h
     int *inv;       // inverse permutation: tree position of original index
     Counters *ctr;
     int cap_nodes, cap_slots, cap_groups, cap_small;
 };
+
+// The set holding particle p (binary search over the set offsets).
+__device__ __forceinline__ int find_set(const int *set_start, int nsets, int p)
+{
+    int lo = 0, hi = nsets - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (set_start[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 // Load particle p of the level's source: the input arrays (root level) or a
 // working buffer.

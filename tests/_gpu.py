@@ -34,14 +34,14 @@ def run_gpu(s, bucket_size=16, ngmax=256, alpha=0.5, beta=0.5, density=False, tr
     return out
 
 
-def canonical_tree_gpu(e, n):
+def canonical_tree_gpu(e, n, root=0, off=0):
     """Per-internal-cell table and per-particle (cell, sub-cell id) from the
-    GPU export."""
+    GPU export; `root` is the set's root node, `off` its first particle."""
     return _canon(e["lo"], e["hi"], e["depth"], e["b"], e["count"],
-                  lambda i: _gpu_children(e, i), n)
+                  lambda i: _gpu_children(e, i, off), n, root)
 
 
-def _gpu_children(e, i):
+def _gpu_children(e, i, off=0):
     b = int(e["b"][i])
     k0 = int(e["slot0"][i])
     out = []
@@ -51,7 +51,7 @@ def _gpu_children(e, i):
         if c >= 0 and int(e["b"][c]) > 0:
             out.append((j, ("node", c)))
         else:
-            out.append((j, ("leaf", e["order"][st:st + ct])))
+            out.append((j, ("leaf", e["order"][st:st + ct] - off)))
     return out
 
 
@@ -74,7 +74,7 @@ def _orc_children(e, i):
     return out
 
 
-def _canon(lo, hi, depth, b, count, children, n):
+def _canon(lo, hi, depth, b, count, children, n, root=0):
     """Walk from the root: cells keyed by (depth, lo, hi); for each internal
     cell its b and count; for each particle the key of its parent cell and its
     sub-cell id."""
@@ -82,10 +82,10 @@ def _canon(lo, hi, depth, b, count, children, n):
     pcell = np.full(n, -1, np.int64)
     pj = np.full(n, -1, np.int64)
     keys = []
-    stack = [0]
+    stack = [root]
     if n == 0:
         return cells, pcell, pj, keys
-    if int(b[0]) == 0:
+    if int(b[root]) == 0:
         keys.append(("leafroot",))
         pcell[:] = 0
         pj[:] = 0
@@ -105,8 +105,8 @@ def _canon(lo, hi, depth, b, count, children, n):
     return cells, pcell, pj, keys
 
 
-def compare_trees(gpu_export, orc_export, n):
-    gc, gp, gj, gk = canonical_tree_gpu(gpu_export, n)
+def compare_trees(gpu_export, orc_export, n, root=0, off=0):
+    gc, gp, gj, gk = canonical_tree_gpu(gpu_export, n, root, off)
     oc, op_, oj, ok = canonical_tree_oracle(orc_export, n)
     assert gc == oc, "internal cells (depth, box, b, count) differ"
     # map cell indices through their keys

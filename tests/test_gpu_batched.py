@@ -1,0 +1,157 @@
+"""Batched BuildTree: many independent, uneven particle sets in one build
+(btree_build_batched), searched and summed by the same find / density calls.
+
+Each set's tree must be the oracle's tree of that set alone (Algorithm 1 with
+the set's own s, alpha, beta, or the octree of Sec. 2), and its neighbour
+lists, counts and densities must be identical -- bit for bit, densities
+included -- to those of the same set built and searched alone.
+"""
+import numpy as np
+import pytest
+
+from paper_1910_02639_gb300 import workloads as wl
+from tests._gpu import compare_trees, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+NGMAX = 256
+
+
+@pytest.fixture(scope="module")
+def bt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1910_02639_gb300 as m
+    return m
+
+
+def _concat(sets):
+    off = np.zeros(len(sets) + 1, np.int64)
+    off[1:] = np.cumsum([s.n for s in sets])
+    cat = lambda k: np.concatenate([getattr(s, k) for s in sets]).astype(np.float32)
+    return off, cat("x"), cat("y"), cat("z"), cat("h"), cat("m")
+
+
+def run_batched(bt, sets, params=None, ngmax=NGMAX):
+    import torch
+    dev = torch.device("cuda:0")
+    off, *arrs = _concat(sets)
+    x, y, z, h, m = (torch.from_numpy(a).to(dev) for a in arrs)
+    n = int(off[-1])
+    tree = bt.btree_build_batched(x, y, z, h, off, params)
+    nb = torch.full((max(n, 1) * ngmax,), -1, dtype=torch.int32, device=dev)
+    cnt = torch.full((max(n, 1),), -7, dtype=torch.int32, device=dev)
+    rho = torch.empty(max(n, 1), dtype=torch.float32, device=dev)
+    bt.btree_find_neighbors_density(tree, m, ngmax, nb, cnt, rho)
+    torch.cuda.synchronize()
+    nbh = nb.view(-1, ngmax)[:n].cpu().numpy()
+    cnth, rhoh = cnt[:n].cpu().numpy(), rho[:n].cpu().numpy()
+    out = [dict(nb=nbh[off[i]:off[i + 1]], cnt=cnth[off[i]:off[i + 1]],
+                rho=rhoh[off[i]:off[i + 1]]) for i in range(len(sets))]
+    return tree, off, out
+
+
+def _coincident(n):
+    return wl._pack(np.full(n, 0.25), np.full(n, -1.0), np.full(n, 3.0), np.full(n, 0.1),
+                    name="coincident")
+
+
+def _mixed_sets():
+    """Every path of the builder in one batch: empty set, one particle, a set
+    that is one leaf (n = s), the warp builder (<= 256), big cells, clustered
+    and flat sets, coincident particles."""
+    return [
+        wl.evrard(40_000, seed=501, target=60),
+        wl._pack(np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0)),
+        wl.uniform_cube(1, seed=502),
+        wl.uniform_cube(16, seed=503, target=10),
+        wl.uniform_cube(17, seed=504, target=10),
+        wl.plummer(200, seed=505, target=40),
+        wl.uniform_cube(257, seed=506, target=50),
+        _coincident(40),
+        wl.plummer(30_000, seed=507, target=80),
+        wl.jittered_slab(40, 25, 1, jitter=0.1, h=1.5, seed=508),
+        wl.uniform_cube(9_000, seed=509, target=120),
+        wl.sphere_1r(3_000, seed=510, target=100),
+    ]
+
+
+def _assert_same(a, b, what):
+    assert np.array_equal(a["cnt"], b["cnt"]), what + ": counts"
+    assert np.array_equal(a["nb"], b["nb"]), what + ": lists"
+    assert np.array_equal(a["rho"].view(np.int32), b["rho"].view(np.int32)), what + ": densities"
+
+
+def test_batched_equals_each_set_alone(bt):
+    sets = _mixed_sets()
+    tree, off, res = run_batched(bt, sets)
+    info = bt.btree_get_info(tree)
+    assert info["n"] == off[-1]
+    tree.free()
+    for i, s in enumerate(sets):
+        if s.n == 0:
+            continue
+        alone = run_gpu(s, bucket_size=16, ngmax=NGMAX, density=True)
+        alone["tree"].free()
+        _assert_same(res[i], alone, "set %d (%s, n=%d)" % (i, s.name, s.n))
+
+
+def test_batched_trees_match_the_oracle_per_set(bt, oracle):
+    sets = _mixed_sets()
+    params = [dict(bucket_size=(16, 5, 1, 8)[i % 4], beta=(0.5, 0.0, 1.0)[i % 3],
+                   octree=(i % 5 == 2)) for i in range(len(sets))]
+    tree, off, res = run_batched(bt, sets, params)
+    e = bt.btree_export(tree)
+    tree.free()
+    for i, (s, p) in enumerate(zip(sets, params)):
+        ot = oracle.OracleTree(s.x, s.y, s.z, bucket_size=p["bucket_size"], beta=p["beta"],
+                               octree=p["octree"])
+        compare_trees(e, ot.export(), s.n, root=i, off=int(off[i]))
+        ref_nb, ref_cnt = oracle.find_brute(s.x, s.y, s.z, s.h, NGMAX)
+        assert np.array_equal(res[i]["cnt"], ref_cnt), "set %d counts" % i
+        used = np.arange(NGMAX)[None, :] < np.minimum(ref_cnt, NGMAX)[:, None]
+        assert np.array_equal(np.where(used, ref_nb, -1), res[i]["nb"]), "set %d lists" % i
+
+
+def test_octree_sets_give_the_btree_lists(bt):
+    sets = [wl.evrard(50_000, seed=511, target=80), wl.plummer(20_000, seed=512, target=60)]
+    _, _, bres = run_batched(bt, sets, dict(bucket_size=16))
+    _, _, ores = run_batched(bt, sets, dict(bucket_size=16, octree=True))
+    for i in range(len(sets)):
+        assert np.array_equal(bres[i]["cnt"], ores[i]["cnt"])
+        assert np.array_equal(bres[i]["nb"], ores[i]["nb"])
+
+
+def test_many_uneven_sets_density_matches_oracle(bt, oracle):
+    # 48 sets, log-uniform sizes 100 .. 30000, the kinds of the batched workload
+    sets = wl.batched_sets(48, seed=513, nmin=100, nmax=30_000)
+    _, off, res = run_batched(bt, sets)
+    for i, s in enumerate(sets):
+        ot = oracle.OracleTree(s.x, s.y, s.z, bucket_size=16)
+        nb, cnt = ot.find(s.h, NGMAX)
+        assert np.array_equal(res[i]["cnt"], cnt), "set %d counts" % i
+        rho = ot.density(s.h, s.m)
+        rel = np.abs(res[i]["rho"].astype(np.float64) - rho) / rho
+        assert rel.max() < 1e-5, "set %d density" % i
+
+
+def test_batched_order_of_sets_does_not_matter(bt):
+    sets = wl.batched_sets(12, seed=514, nmin=50, nmax=20_000)
+    _, _, a = run_batched(bt, sets)
+    perm = np.random.default_rng(5).permutation(len(sets))
+    _, _, b = run_batched(bt, [sets[k] for k in perm])
+    for j, k in enumerate(perm):
+        _assert_same(a[k], b[j], "set %d" % k)
+
+
+def test_batched_argument_errors(bt):
+    import torch
+    x = torch.zeros(10, device="cuda:0")
+    with pytest.raises(ValueError):
+        bt.btree_build_batched(x, x, x, x, [0, 5, 9])
+    with pytest.raises(bt.BtreeError) as ei:
+        bt.btree_build_batched(x, x, x, x, [0, 6, 5, 10])
+    assert ei.value.status == bt.BT_ERR_ARG
+    with pytest.raises(bt.BtreeError):
+        bt.btree_build_batched(x, x, x, x, [0, 10], dict(bucket_size=0))

@@ -353,3 +353,30 @@ def test_density_lattice_is_riemann_sum_of_unit_integral(oracle):
     i = 5 + 11 * (5 + 11 * 5)
     # sum_v W(|v|, h) over the unit lattice approximates the integral of W = 1
     assert abs(rho[i] * s.n - 1.0) < 0.01
+
+
+# --------------------------------------------------------------- octree mode
+def test_octree_mode_is_the_perfect_octree_on_a_power_of_two_lattice(oracle):
+    # 8x8x8 unit lattice, box [0,7]^3, s = 1: every split halves at the cell
+    # middle, 4 lattice points per side -> depth 3, 1 + 8 + 64 internal cells,
+    # every leaf one particle
+    s = wl.lattice(8, 8, 8, h=0.5)
+    t = oracle.OracleTree(s.x, s.y, s.z, bucket_size=1, octree=True)
+    e = t.export()
+    internal = e["b"] > 0
+    assert np.all(e["b"][internal] == 2)
+    assert internal.sum() == 73 and t.max_depth == 3
+    leaf = ~internal
+    assert np.all(e["count"][leaf] == 1)
+    # the b-tree of the same lattice is one level (b0 = 8)
+    tb = oracle.OracleTree(s.x, s.y, s.z, bucket_size=1)
+    assert tb.export()["b"][0] == 8 and tb.max_depth == 1
+
+
+def test_octree_and_btree_give_the_same_lists(oracle):
+    s = wl.evrard(5000, seed=91, target=60)
+    a = oracle.OracleTree(s.x, s.y, s.z, bucket_size=8, octree=True).find(s.h, 256)
+    b = oracle.OracleTree(s.x, s.y, s.z, bucket_size=8).find(s.h, 256)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    _check_tree_invariants(oracle.OracleTree(s.x, s.y, s.z, bucket_size=8, octree=True).export(),
+                           s.n, 8)
