@@ -266,6 +266,10 @@ def run_gpu(args):
            "gpu_launches": int(launches),
            "clocks": sampler.summary(t0, t1)}
 
+    # ---- many uneven sets: batched vs the plain per-set path
+    if not args.no_batched:
+        out["batched"] = run_batched_section(args, bt, dev, stream, dist, rank, ws)
+
     # ---- end to end through the public API, host buffers
     if not args.no_e2e:
         out["e2e"] = run_e2e(args, bt, s, cfg, dev, stream, dist, ws, pairs)
@@ -318,6 +322,83 @@ def run_e2e(args, bt, s, cfg, dev, stream, dist, ws, pairs):
     del h_nb
     return {"value": pairs * ws / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": K,
             "h2d_bytes_per_step": 5 * 4 * n, "d2h_bytes_per_step": 4 * n * ngmax + 8 * n}
+
+
+# ---------------------------------------------------------------- batched sets
+def _timed(fn, stream, steps, warmup=3):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_batched_section(args, bt, dev, stream, dist, rank, ws):
+    """256 independent sets, sizes log-uniform in [1e3, 1e6] (uniform cube,
+    1/r sphere, Plummer; 50-150 target neighbours), ngmax 256.  Each rank
+    takes a size-balanced share of the sets (no collective on the data path).
+    Three forms on the same sets, same outputs: the plain path (build + find
+    per set), one batched call with the default parameters, one batched call
+    with the autotuner's per-size-class parameters."""
+    import torch
+    from paper_1910_02639_gb300 import workloads as wl
+    from paper_1910_02639_gb300.autotune import Tuner
+    from paper_1910_02639_gb300.batch import DeviceSets, list_checksum, shard_sets
+    specs = wl.batched_specs(args.batched_sets, seed=1914)
+    mine = shard_sets([sp[1] for sp in specs], ws)[rank]
+    sets = [wl.make_set(*specs[i]) for i in mine]
+    ngmax = 256
+    ds = DeviceSets(sets, dev, ngmax)
+    K = args.batched_steps
+    t0 = time.time()
+    tuner = Tuner(dev, ngmax, stream=stream)
+    tuner.tune(sets)
+    tune_s = time.time() - t0
+    tuned = tuner.params_for(sets)
+
+    plain_ms = _timed(lambda: ds.run_plain(None, stream), stream, K)
+    ref = (int(ds.cnt.to(torch.int64).sum().item()), list_checksum(ds.nb, ds.cnt, ngmax))
+    rho_ref = ds.rho.clone()
+    l0 = bt.btree_kernel_launches()
+    batched_ms = _timed(lambda: ds.run_batched(None, stream), stream, K)
+    launches_batched = (bt.btree_kernel_launches() - l0) // (K + 3)
+    same_b = ((int(ds.cnt.to(torch.int64).sum().item()), list_checksum(ds.nb, ds.cnt, ngmax)) == ref
+              and torch.equal(ds.rho, rho_ref))
+    tuned_ms = _timed(lambda: ds.run_batched(tuned, stream), stream, K)
+    same_t = ((int(ds.cnt.to(torch.int64).sum().item()), list_checksum(ds.nb, ds.cnt, ngmax)) == ref
+              and torch.equal(ds.rho, rho_ref))
+    pairs = ref[0]
+    all_pairs = pairs
+    if dist:
+        t = torch.tensor([pairs], dtype=torch.float64, device=dev)
+        dist.all_reduce(t)
+        all_pairs = int(t.item())
+    plain_ms, batched_ms, tuned_ms = (reduce_max(dist, v, dev) for v in (plain_ms, batched_ms, tuned_ms))
+    ds.free()
+    rate = lambda ms: all_pairs / (ms * 1e-3)
+    table = {str(k): {kk: v[kk] for kk in ("bucket_size", "beta", "group_size")}
+             for k, v in tuner.table.items()}
+    return {"workload": f"batched_{args.batched_sets}_sets", "n": int(sum(sp[1] for sp in specs)),
+            "nsets": len(specs), "ngmax": ngmax, "scaling": "strong", "sets_per_rank": len(mine),
+            "pairs_per_step": all_pairs, "unit": UNIT,
+            "plain": {"value": rate(plain_ms), "ms_per_step": plain_ms,
+                      "form": "btree_build + fused find per set, s=16, beta=0.5"},
+            "batched": {"value": rate(batched_ms), "ms_per_step": batched_ms,
+                        "launches_per_step": int(launches_batched),
+                        "form": "btree_build_batched + one fused find, s=16, beta=0.5",
+                        "identical_to_plain": bool(same_b)},
+            "tuned": {"value": rate(tuned_ms), "ms_per_step": tuned_ms,
+                      "identical_to_plain": bool(same_t), "table": table,
+                      "tuning_s": round(tune_s, 2), "trials": tuner.trials},
+            "speedup_batched_vs_plain": plain_ms / batched_ms,
+            "speedup_tuned_vs_plain": plain_ms / tuned_ms,
+            "steps": K, "warmup": 3}
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -395,6 +476,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--ref-sample", type=int, default=200_000)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-sets", type=int, default=256)
+    ap.add_argument("--batched-steps", type=int, default=5)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -122,6 +122,10 @@ typedef struct {
     int flags;       /* 0 or BT_SET_OCTREE                      */
     double alpha;    /* underfull fraction (Eq. 4), e.g. 0.5    */
     double beta;     /* empty-cell limit (Eq. 4), e.g. 0.5      */
+    int group_size;  /* queries searched together (a find work
+                        unit; leaves are split to fit), 1..32,
+                        0 = 32.  Changes speed, never results.  */
+    int reserved;    /* 0                                       */
 } bt_set_params;
 
 /*

@@ -180,14 +180,16 @@ BT_SET_OCTREE = 1
 
 class _SetParams(ctypes.Structure):
     _fields_ = [("bucket_size", ctypes.c_int), ("flags", ctypes.c_int),
-                ("alpha", ctypes.c_double), ("beta", ctypes.c_double)]
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("group_size", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 def btree_build_batched(x, y, z, h, offsets, params=None, stream=None,
                         tree: Tree | None = None) -> Tree:
     """BuildTree for many sets at once.  x, y, z, h: the sets concatenated;
     offsets: nsets+1 ints; params: per-set dicts with bucket_size, alpha,
-    beta, octree (or one dict for all, or None for the defaults)."""
+    beta, octree, group_size (or one dict for all, or None for the
+    defaults)."""
     import torch
     lib = _load()
     n = int(x.numel())
@@ -206,6 +208,7 @@ def btree_build_batched(x, y, z, h, offsets, params=None, stream=None,
             c_par[i].flags = BT_SET_OCTREE if p.get("octree", False) else 0
             c_par[i].alpha = float(p.get("alpha", 0.5))
             c_par[i].beta = float(p.get("beta", 0.5))
+            c_par[i].group_size = int(p.get("group_size", 0))
     t = tree if tree is not None else Tree()
     st = lib.btree_build_batched(*ptrs, c_offs, nsets, c_par, None,
                                  ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(t._ptr))

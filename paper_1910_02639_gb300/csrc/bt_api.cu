@@ -50,10 +50,11 @@ struct btree {
     float *smass = nullptr;
     // per-set tables (device) and their pinned host staging
     int nsets = 0, cap_sets = 0;
-    int *set_start = nullptr, *set_s = nullptr, *set_na = nullptr, *set_thr = nullptr;
-    int *set_flags = nullptr, *set_flags_in = nullptr, *set_bbox = nullptr;
-    int *h_sets = nullptr;  // [4 * cap_sets + 1]: start[n+1], s[n], na[n], flags[n]
-    int *h_thr = nullptr;   // [cap_sets * (kMaxB + 1)]
+    int *set_start = nullptr, *set_s = nullptr, *set_na = nullptr, *set_gmax = nullptr;
+    int *set_flags = nullptr, *set_bbox = nullptr;
+    double *set_beta = nullptr;
+    SetRec *set_rec = nullptr;  // device copy of the staged records
+    SetRec *h_rec = nullptr;    // [cap_sets] pinned staging
 
     int ngroups = 0;
     bt_info info{};
@@ -110,10 +111,12 @@ void free_all(btree *t)
     for (int k = 0; k < 2; k++) { dev_free(t, t->wpos[k]); dev_free(t, t->wh[k]); dev_free(t, t->big_ids[k]); }
     dev_free(t, t->hist); dev_free(t, t->hoff); dev_free(t, t->cursor); dev_free(t, t->tiles);
     dev_free(t, t->big); dev_free(t, t->small); dev_free(t, t->ctr); dev_free(t, t->smass);
-    dev_free(t, t->set_start); dev_free(t, t->set_s); dev_free(t, t->set_na); dev_free(t, t->set_thr);
-    dev_free(t, t->set_flags); dev_free(t, t->set_flags_in); dev_free(t, t->set_bbox);
-    t->set_start = t->set_s = t->set_na = t->set_thr = nullptr;
-    t->set_flags = t->set_flags_in = t->set_bbox = nullptr;
+    dev_free(t, t->set_start); dev_free(t, t->set_s); dev_free(t, t->set_na); dev_free(t, t->set_gmax);
+    dev_free(t, t->set_flags); dev_free(t, t->set_bbox); dev_free(t, t->set_beta); dev_free(t, t->set_rec);
+    t->set_start = t->set_s = t->set_na = t->set_gmax = nullptr;
+    t->set_flags = t->set_bbox = nullptr;
+    t->set_beta = nullptr;
+    t->set_rec = nullptr;
     t->cap_sets = 0;
     t->geom = nullptr; t->walk = nullptr; t->slots = nullptr; t->groups = nullptr;
     t->spos = nullptr; t->sh = nullptr; t->inv = nullptr;
@@ -132,7 +135,8 @@ TreeDev view(const btree *t)
     T.set_start = t->set_start;
     T.set_s = t->set_s;
     T.set_na = t->set_na;
-    T.set_thr = t->set_thr;
+    T.set_beta = t->set_beta;
+    T.set_gmax = t->set_gmax;
     T.set_flags = t->set_flags;
     T.set_bbox = t->set_bbox;
     T.geom = t->geom;
@@ -219,17 +223,14 @@ int ensure_set_caps(btree *t, int nsets)
     if (t->cap_sets >= nsets && t->set_start) return BT_OK;
     const int c = std::max(nsets, 1);
     if (!realloc_dev(t, t->set_start, 0, c + 1, false) || !realloc_dev(t, t->set_s, 0, c, false) ||
-        !realloc_dev(t, t->set_na, 0, c, false) ||
-        !realloc_dev(t, t->set_thr, 0, (int64_t)c * (kMaxB + 1), false) ||
-        !realloc_dev(t, t->set_flags, 0, c, false) || !realloc_dev(t, t->set_flags_in, 0, c, false) ||
-        !realloc_dev(t, t->set_bbox, 0, 6 * c, false))
+        !realloc_dev(t, t->set_na, 0, c, false) || !realloc_dev(t, t->set_gmax, 0, c, false) ||
+        !realloc_dev(t, t->set_beta, 0, c, false) || !realloc_dev(t, t->set_rec, 0, c, false) ||
+        !realloc_dev(t, t->set_flags, 0, c, false) || !realloc_dev(t, t->set_bbox, 0, 6 * c, false))
         return BT_ERR_OOM;
-    if (t->h_sets) cudaFreeHost(t->h_sets);
-    if (t->h_thr) cudaFreeHost(t->h_thr);
-    t->h_sets = nullptr;
-    t->h_thr = nullptr;
-    if (cudaMallocHost(&t->h_sets, sizeof(int) * (4 * (size_t)c + 1)) != cudaSuccess ||
-        cudaMallocHost(&t->h_thr, sizeof(int) * (size_t)c * (kMaxB + 1)) != cudaSuccess) {
+    // the previous build has finished reading the staging (builds end synchronised)
+    if (t->h_rec) cudaFreeHost(t->h_rec);
+    t->h_rec = nullptr;
+    if (cudaMallocHost(&t->h_rec, sizeof(SetRec) * (size_t)c) != cudaSuccess) {
         cudaGetLastError();
         return BT_ERR_OOM;
     }
@@ -253,14 +254,10 @@ int do_build(btree *t, const float *x, const float *y, const float *z, const flo
     cudaStream_t st = t->st;
     TreeDev T = view(t);
     // per-set tables (staged on the host by the caller)
-    cudaMemcpyAsync(t->set_start, t->h_sets, sizeof(int) * (ns + 1), cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(t->set_s, t->h_sets + (ns + 1), sizeof(int) * ns, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(t->set_na, t->h_sets + (2 * ns + 1), sizeof(int) * ns, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(t->set_flags_in, t->h_sets + (3 * ns + 1), sizeof(int) * ns, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(t->set_thr, t->h_thr, sizeof(int) * (size_t)ns * (kMaxB + 1), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(t->set_rec, t->h_rec, sizeof(SetRec) * (size_t)ns, cudaMemcpyHostToDevice, st);
     launch_init_counters(t->ctr, st);
     launch_set_int(&t->ctr->nnodes, ns, st);  // nodes 0..ns-1 are the roots
-    launch_init_sets(T, t->set_flags_in, st);
+    launch_init_sets(T, t->set_rec, t->set_start, t->set_s, t->set_na, t->set_beta, t->set_gmax, st);
     cudaEventRecord(t->ev0, st);
     launch_bbox(T, x, y, z, h, t->sms, st);
     launch_root_sets(T, t->big_ids[0], t->small, st);
@@ -350,7 +347,7 @@ bool is_finite_d(double v) { return std::isfinite(v); }
 }  // namespace
 
 // Shared front end of btree_build and btree_build_batched: the per-set
-// tables must already be staged in t->h_sets / t->h_thr.
+// records must already be staged in t->h_rec.
 static int build_core(btree *t, const float *x, const float *y, const float *z, const float *h)
 {
     int rc = BT_OK;
@@ -420,21 +417,18 @@ static btree *prepare_handle(btree_t **out, const bt_allocator *alloc, void *str
     return t;
 }
 
-// Eq. 4 integer bounds of one set: n_j <= alpha*s in binary64 is n_j <= na;
-// halving iff u > beta*b^3 in binary64 is u > thr[b] (u, n_j integers).
-static void stage_set(btree *t, int i, int ns, int s, double alpha, double beta, int flags)
+static void stage_set(btree *t, int i, int64_t start, int64_t end, int s, double alpha, double beta,
+                      int flags, int gmax)
 {
-    const double under = alpha * (double)s;
-    const int na = under < 0.0 ? -1 : (under >= 2147483647.0 ? INT32_MAX : (int)std::floor(under));
-    t->h_sets[(ns + 1) + i] = s;
-    t->h_sets[(2 * ns + 1) + i] = na;
-    t->h_sets[(3 * ns + 1) + i] = flags;
-    int *thr = t->h_thr + (size_t)i * (kMaxB + 1);
-    for (int b = 0; b <= kMaxB; b++) {
-        const double bb = (double)b * (double)b * (double)b;
-        const double v = beta * bb;
-        thr[b] = v < 0.0 ? -1 : (v >= 2147483647.0 ? INT32_MAX : (int)std::floor(v));
-    }
+    SetRec &r = t->h_rec[i];
+    r.start = (int)start;
+    r.end = (int)end;
+    r.s = s;
+    r.flags = flags;
+    r.gmax = gmax;
+    r.pad = 0;
+    r.alpha = alpha;
+    r.beta = beta;
 }
 
 extern "C" {
@@ -457,9 +451,7 @@ int btree_build(const float *x, const float *y, const float *z, const float *h, 
     t->beta = beta;
     t->nsets = 1;
     if ((rc = ensure_set_caps(t, 1)) != BT_OK) return rc;
-    t->h_sets[0] = 0;
-    t->h_sets[1] = (int)n;
-    stage_set(t, 0, 1, bucket_size, alpha, beta, 0);
+    stage_set(t, 0, 0, n, bucket_size, alpha, beta, 0, kGroupMax);
     return build_core(t, x, y, z, h);
 }
 
@@ -481,6 +473,7 @@ int btree_build_batched(const float *x, const float *y, const float *z, const fl
         const double a = params ? params[i].alpha : 0.5, b = params ? params[i].beta : 0.5;
         if (s < 1 || s > (1 << 20) || !is_finite_d(a) || !is_finite_d(b)) return BT_ERR_ARG;
         if (params && (params[i].flags & ~BT_SET_OCTREE)) return BT_ERR_ARG;
+        if (params && (params[i].group_size < 0 || params[i].group_size > kGroupMax)) return BT_ERR_ARG;
         smin = std::min(smin, s);
     }
     int rc;
@@ -492,12 +485,12 @@ int btree_build_batched(const float *x, const float *y, const float *z, const fl
     t->beta = params ? params[0].beta : 0.5;
     t->nsets = nsets;
     if ((rc = ensure_set_caps(t, nsets)) != BT_OK) return rc;
-    for (int i = 0; i <= nsets; i++) t->h_sets[i] = (int)offsets[i];
     for (int i = 0; i < nsets; i++) {
         const int s = params ? params[i].bucket_size : 16;
         const double a = params ? params[i].alpha : 0.5, b = params ? params[i].beta : 0.5;
         const int f = params && (params[i].flags & BT_SET_OCTREE) ? kSetOctree : 0;
-        stage_set(t, i, nsets, s, a, b, f);
+        const int g = params && params[i].group_size > 0 ? params[i].group_size : kGroupMax;
+        stage_set(t, i, offsets[i], offsets[i + 1], s, a, b, f, g);
     }
     return build_core(t, x, y, z, h);
 }
@@ -646,8 +639,7 @@ void btree_free(btree_t *t)
     if (!t) return;
     free_all(t);
     if (t->hctr) cudaFreeHost(t->hctr);
-    if (t->h_sets) cudaFreeHost(t->h_sets);
-    if (t->h_thr) cudaFreeHost(t->h_thr);
+    if (t->h_rec) cudaFreeHost(t->h_rec);
     if (t->ev0) cudaEventDestroy(t->ev0);
     if (t->ev1) cudaEventDestroy(t->ev1);
     delete t;

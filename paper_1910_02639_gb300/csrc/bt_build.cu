@@ -21,14 +21,16 @@
 
 namespace bt {
 
+// Work units of at most the set's gmax particles over tree positions
+// [start, start + cnt).
 __device__ __forceinline__ void emit_groups(const TreeDev &T, int set, int start, int cnt)
 {
-    const int ng = (cnt + kGroupMax - 1) / kGroupMax;
+    const int gm = T.set_gmax[set];
+    const int ng = (cnt + gm - 1) / gm;
     const int g0 = atomicAdd(&T.ctr->ngroups, ng);
     for (int q = 0; q < ng; q++)
         if (g0 + q < T.cap_groups)
-            T.groups[g0 + q] = make_int2(start + q * kGroupMax,
-                                         group_pack(set, min(kGroupMax, cnt - q * kGroupMax)));
+            T.groups[g0 + q] = make_int2(start + q * gm, group_pack(set, min(gm, cnt - q * gm)));
     if (g0 + ng > T.cap_groups) atomicOr(&T.ctr->status, kStCapGroups);
 }
 
@@ -113,14 +115,26 @@ __global__ void __launch_bounds__(256) k_bbox(const float *__restrict__ x,
     if (__any_sync(~0u, bad) && (threadIdx.x & 31) == 0) atomicOr(&ctr->status, kStNonfinite);
 }
 
-__global__ void k_init_sets(int *set_bbox, int *set_flags, const int *flags_in, int nsets)
+// Per-set tables from the staged records.  n_j <= alpha*s (binary64) is
+// n_j <= floor(alpha*s) for integer n_j.
+__global__ void k_init_sets(TreeDev T, const SetRec *rec, int *set_start, int *set_s, int *set_na,
+                            double *set_beta, int *set_gmax)
 {
+    const int nsets = T.nsets;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsets; s += gridDim.x * blockDim.x) {
+        const SetRec r = rec[s];
         for (int l = 0; l < 3; l++) {
-            set_bbox[6 * s + l] = INT_MAX;
-            set_bbox[6 * s + 3 + l] = INT_MIN;
+            T.set_bbox[6 * s + l] = INT_MAX;
+            T.set_bbox[6 * s + 3 + l] = INT_MIN;
         }
-        set_flags[s] = flags_in[s];
+        set_start[s] = r.start;
+        if (s == nsets - 1) set_start[nsets] = r.end;
+        set_s[s] = r.s;
+        const double under = __dmul_rn(r.alpha, (double)r.s);
+        set_na[s] = under < 0.0 ? -1 : (under >= 2147483647.0 ? INT_MAX : (int)floor(under));
+        set_beta[s] = r.beta;
+        set_gmax[s] = r.gmax;
+        T.set_flags[s] = r.flags;
     }
 }
 
@@ -363,7 +377,7 @@ __global__ void k_big_decide(TreeDev T, BigCell *big, int nb)
     BigCell &c = big[i];
     c.halved = 0;
     if (c.state != 0) return;
-    if (c.u > T.set_thr[c.set * (kMaxB + 1) + c.b] && c.b > 2) {
+    if (c.b > 2 && ratio_halves(T, c.set, c.u, c.b)) {
         c.b = max(2, c.b / 2);
         c.halved = 1;
         c.u = 0;
@@ -640,7 +654,6 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
         const int set = G.set;
         const int s_set = T.set_s[set];
         const int na = T.set_na[set];
-        const int *thr = T.set_thr + set * (kMaxB + 1);
         const bool octree = (T.set_flags[set] & kSetOctree) != 0;
         const Src &src = item.src == 0 ? src0 : (item.src == 1 ? src1 : srcin);
         for (int k = lane; k < m0; k += 32) {
@@ -685,7 +698,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                     int u = 0;
                     for (int j = lane; j < ncell; j += 32) u += S.hist[j] <= na;
                     u = warp_sum(u);
-                    if (u > thr[b] && b > 2) {
+                    if (b > 2 && ratio_halves(T, set, u, b)) {
                         b = max(2, b / 2);
                         __syncwarp();
                         continue;
@@ -745,7 +758,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                 __syncwarp();
                 // a cell of <= kWholeMax particles becomes work units of its own
                 if (F.eself && lane == 0) {
-                    if (m <= kGroupMax) {
+                    if (m <= T.set_gmax[set]) {
                         emit_groups(T, set, base + a, m);
                     } else {
                         // two units split at the sub-cell boundary nearest the
@@ -884,10 +897,12 @@ static inline int grid_for(long long work, int per_block, int max_blocks)
     return (int)g;
 }
 
-void launch_init_sets(const TreeDev &T, const int *flags_in, cudaStream_t st)
+void launch_init_sets(const TreeDev &T, const SetRec *rec, int *set_start, int *set_s, int *set_na,
+                      double *set_beta, int *set_gmax, cudaStream_t st)
 {
     note_launch();
-    k_init_sets<<<grid_for(T.nsets, 256, 1 << 16), 256, 0, st>>>(T.set_bbox, T.set_flags, flags_in, T.nsets);
+    k_init_sets<<<grid_for(T.nsets, 256, 1 << 16), 256, 0, st>>>(T, rec, set_start, set_s, set_na,
+                                                                 set_beta, set_gmax);
 }
 
 void launch_bbox(const TreeDev &T, const float *x, const float *y, const float *z, const float *h,

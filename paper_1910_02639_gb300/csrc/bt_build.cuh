@@ -4,7 +4,8 @@
 
 namespace bt {
 
-void launch_init_sets(const TreeDev &T, const int *flags_in, cudaStream_t st);
+void launch_init_sets(const TreeDev &T, const SetRec *rec, int *set_start, int *set_s, int *set_na,
+                      double *set_beta, int *set_gmax, cudaStream_t st);
 void launch_bbox(const TreeDev &T, const float *x, const float *y, const float *z, const float *h,
                  int sms, cudaStream_t st);
 void launch_root_sets(const TreeDev &T, int *big_ids, SmallItem *small, cudaStream_t st);

@@ -71,7 +71,8 @@ struct FindSmem {
     int hist[256];
     float box[13];            // PL[3] PH[3] QL[3] QH[3] T
     int njobs, nfront, nnext, ncand, kmin, kmax, range_ovf, ovf_lo, ovf_hi;
-    int jfail, cover, gstart, gcount, whi;
+    int jfail, cover, gstart, gcount, whi, ctot;
+    int wcnt[2][kFindWarps];  // per-warp kept counts (scan mode), double-buffered
     int gset, set_lo, set_hi;  // the group's particle set and its index range
 };
 
@@ -113,6 +114,7 @@ __device__ __forceinline__ void add_range(FindSmem &S, int s, int len)
 {
     if (len <= 0) return;
     const int nj = (len + 31) >> 5;
+    atomicAdd(&S.ctot, len);
     const int j0 = atomicAdd(&S.njobs, nj);
     if (j0 + nj <= kJobMax) {
         for (int k = 0; k < nj; k++) S.jobs[j0 + k] = make_int2(s + 32 * k, min(32, len - 32 * k));
@@ -133,6 +135,7 @@ __device__ void group_walk(const TreeDev &T, FindSmem &S)
     const int tid = threadIdx.x;
     if (tid == 0) {
         S.njobs = 0;
+        S.ctot = 0;
         S.cover = 0;
         S.range_ovf = 0;
         S.jfail = kJobMax;
@@ -252,6 +255,7 @@ __device__ void group_walk(const TreeDev &T, FindSmem &S)
             if (tid == 0) {
                 S.jobs[0] = make_int2(lo, hi - lo);
                 S.njobs = (hi - lo + 31) >> 5;
+                S.ctot = hi - lo;
                 S.cover = 1;
                 atomicOr(&T.ctr->status, kStWalk);
             }
@@ -380,31 +384,35 @@ __device__ __forceinline__ void fix_band(FindSmem &S, int c, int gcount, const f
 }
 
 // Sort, test and emit the candidates of the current window.
+// `presorted`: the candidates were collected in ascending original index
+// and their keys are already in S.key (scan mode).
 template <bool DENS>
-__device__ void group_window(const FindArgs &A, FindSmem &S)
+__device__ void group_window(const FindArgs &A, FindSmem &S, bool presorted)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m = S.ncand;  // <= kCap here
     const int gcount = S.gcount;
     if (m == 0) return;
     const int kmin = S.kmin;
-    int npad = kSortThreads;
-    while (npad < m) npad <<= 1;
-    for (int s = tid; s < npad; s += kFindThreads) {
-        uint32_t k = 0xffffffffu;
-        if (s < m) k = ((uint32_t)(__float_as_int(S.cand[s].w) - kmin) << kSlotBits) | (uint32_t)s;
-        S.key[s] = k;
-    }
-    __syncthreads();
-    if (tid < kSortThreads) {
-        switch (npad) {
-        case kSortThreads: sort_keys<1>(S.key); break;
-        case 2 * kSortThreads: sort_keys<2>(S.key); break;
-        case 4 * kSortThreads: sort_keys<4>(S.key); break;
-        default: sort_keys<8>(S.key); break;
+    if (!presorted) {
+        int npad = kSortThreads;
+        while (npad < m) npad <<= 1;
+        for (int s = tid; s < npad; s += kFindThreads) {
+            uint32_t k = 0xffffffffu;
+            if (s < m) k = ((uint32_t)(__float_as_int(S.cand[s].w) - kmin) << kSlotBits) | (uint32_t)s;
+            S.key[s] = k;
         }
+        __syncthreads();
+        if (tid < kSortThreads) {
+            switch (npad) {
+            case kSortThreads: sort_keys<1>(S.key); break;
+            case 2 * kSortThreads: sort_keys<2>(S.key); break;
+            case 4 * kSortThreads: sort_keys<4>(S.key); break;
+            default: sort_keys<8>(S.key); break;
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
     // sorted position of each query itself (it is its own candidate when its
     // original index lies in this window)
     if (tid < gcount) {
@@ -515,6 +523,71 @@ __device__ void group_window(const FindArgs &A, FindSmem &S)
     __syncthreads();
 }
 
+// Scan mode, for a group whose query box holds a large part of its set (very
+// large h): instead of re-streaming the candidates once per window, walk the
+// set in ascending original index through the inverse permutation, keep the
+// particles inside the box, and cut windows of at most kCap candidates that
+// arrive already sorted.  Block-wide: one round = kFindThreads indices.
+template <bool DENS>
+__device__ void group_scan(const FindArgs &A, FindSmem &S)
+{
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const float PL0 = S.box[0], PL1 = S.box[1], PL2 = S.box[2];
+    const float PH0 = S.box[3], PH1 = S.box[4], PH2 = S.box[5];
+    const float T2 = S.box[12];
+    const unsigned lt = (1u << lane) - 1;
+    const int jend = S.set_hi;
+    int j0 = S.set_lo;
+    int buf = 0;
+    while (j0 < jend) {
+        const int kmin = j0;
+        int base = 0;  // candidates kept so far in this window (same in all threads)
+        int j = j0;
+        for (; j < jend; j += kFindThreads) {
+            if (j - kmin > kSpanMax - kFindThreads) break;  // keys must fit their bits
+            const int idx = j + tid;
+            bool keep = false;
+            float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+            float mm = 0.0f;
+            if (idx < jend) {
+                const int p = __ldg(&A.T.inv[idx]);
+                c = __ldg(&A.T.spos[p]);
+                if (DENS) mm = __ldg(&A.smass[p]);
+                const float ex = fmaxf(fmaxf(__fsub_rn(PL0, c.x), __fsub_rn(c.x, PH0)), 0.0f);
+                const float ey = fmaxf(fmaxf(__fsub_rn(PL1, c.y), __fsub_rn(c.y, PH1)), 0.0f);
+                const float ez = fmaxf(fmaxf(__fsub_rn(PL2, c.z), __fsub_rn(c.z, PH2)), 0.0f);
+                keep = fmaf(ez, ez, fmaf(ey, ey, ex * ex)) <= T2;
+            }
+            const unsigned bal = __ballot_sync(~0u, keep);
+            if (lane == 0) S.wcnt[buf][warp] = __popc(bal);
+            __syncthreads();
+            int before = 0, tot = 0;
+#pragma unroll
+            for (int w = 0; w < kFindWarps; w++) {
+                const int v = S.wcnt[buf][w];
+                before += w < warp ? v : 0;
+                tot += v;
+            }
+            buf ^= 1;
+            if (base + tot > kCap) break;  // uniform: this round opens the next window
+            if (keep) {
+                const int slot = base + before + __popc(bal & lt);
+                S.cand[slot] = c;
+                if (DENS) S.cmass[slot] = mm;
+                S.key[slot] = ((uint32_t)(idx - kmin) << kSlotBits) | (uint32_t)slot;
+            }
+            base += tot;
+        }
+        if (tid == 0) {
+            S.ncand = base;
+            S.kmin = kmin;
+        }
+        __syncthreads();
+        group_window<DENS>(A, S, true);
+        j0 = j;
+    }
+}
+
 template <bool DENS>
 __global__ void __launch_bounds__(kFindThreads, 4) k_find(FindArgs A)
 {
@@ -587,10 +660,18 @@ __global__ void __launch_bounds__(kFindThreads, 4) k_find(FindArgs A)
             __syncthreads();
             group_walk(T, S);
 
+            // ---- scan mode when re-streaming the candidates per window would
+            // cost more than one pass over the whole set (C^2 / kCap > 3/4 n)
+            const long long ctot = S.ctot;
+            const long long nset = S.set_hi - S.set_lo;
+            const bool scan = ctot > 2 * kCap && 3 * nset * kCap < 4 * ctot * ctot;
+            if (scan && tid == 0) atomicOr(&T.ctr->status, kStWalk);
+            if (scan) group_scan<DENS>(A, S);
+
             // ---- windows over original index (within the set)
             int wlo = S.set_lo;
-            const int wend = S.set_hi;
-            for (;;) {
+            const int wend = scan ? wlo : S.set_hi;
+            for (; wlo < wend;) {
                 int whi = INT_MAX;
                 if (tid == 0) {
                     S.ncand = 0;
@@ -637,7 +718,7 @@ __global__ void __launch_bounds__(kFindThreads, 4) k_find(FindArgs A)
                     group_gather<DENS>(A, S, 0, wlo, whi, 1);
                     __syncthreads();
                 }
-                group_window<DENS>(A, S);
+                group_window<DENS>(A, S, false);
                 if (whi == INT_MAX || whi >= wend) break;
                 wlo = whi;
             }

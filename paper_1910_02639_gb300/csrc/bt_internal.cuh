@@ -258,6 +258,17 @@ struct SmallItem {
     int src;  // 0/1: working buffer holding its particles; 2: the input arrays
 };
 
+// One set's parameters as staged by the host (copied to the device once per
+// build; k_init_sets derives the per-set tables from it).
+struct SetRec {
+    int start, end;  // particles [start, end)
+    int s;           // bucket size
+    int flags;       // kSetOctree
+    int gmax;        // particles per find work unit, 1..kGroupMax
+    int pad;
+    double alpha, beta;  // Eq. 4
+};
+
 // Per-set flags.
 enum : int {
     kSetOctree = 1,    // b fixed to 2 (no Eq. 1 / Eq. 4): the classical octree
@@ -277,7 +288,8 @@ struct TreeDev {
     const int *set_start;  // [nsets+1] first particle of each set
     const int *set_s;      // [nsets] bucket size s
     const int *set_na;     // [nsets] largest n_j counted as underfull (alpha s, Eq. 4)
-    const int *set_thr;    // [nsets][kMaxB+1]: accept b iff u <= thr (beta b^3, Eq. 4)
+    const double *set_beta;  // [nsets] beta of Eq. 4
+    const int *set_gmax;   // [nsets] particles per find work unit
     int *set_flags;        // [nsets]
     int *set_bbox;         // [nsets][6] ordered-int min x,y,z, max x,y,z
     NodeGeom *geom;
@@ -290,6 +302,14 @@ struct TreeDev {
     Counters *ctr;
     int cap_nodes, cap_slots, cap_groups, cap_small;
 };
+
+// Ratio test of Eq. 4 for a cell of the given set: halve b iff
+// u > beta * b^3, in binary64 (b^3 is exact; u is an integer).
+__device__ __forceinline__ bool ratio_halves(const TreeDev &T, int set, int u, int b)
+{
+    const double bb = (double)(b * b * b);
+    return (double)u > __dmul_rn(T.set_beta[set], bb);
+}
 
 // The set holding particle p (binary search over the set offsets).
 __device__ __forceinline__ int find_set(const int *set_start, int nsets, int p)

@@ -155,3 +155,55 @@ def test_batched_argument_errors(bt):
     assert ei.value.status == bt.BT_ERR_ARG
     with pytest.raises(bt.BtreeError):
         bt.btree_build_batched(x, x, x, x, [0, 10], dict(bucket_size=0))
+
+
+@pytest.mark.parametrize("params", [
+    dict(group_size=8), dict(group_size=16), dict(group_size=1),
+    dict(bucket_size=64, beta=0.25, group_size=16), dict(bucket_size=8, beta=0.75),
+])
+def test_tuning_knobs_never_change_results(bt, params):
+    # s, beta and the work-unit size change the tree and the schedule only:
+    # lists, counts and densities must stay bit-identical
+    sets = wl.batched_sets(10, seed=515, nmin=300, nmax=40_000)
+    _, _, ref = run_batched(bt, sets)
+    _, _, got = run_batched(bt, sets, params)
+    for i in range(len(sets)):
+        _assert_same(got[i], ref[i], "set %d with %s" % (i, params))
+
+
+def test_plain_path_helper_matches_batched(bt):
+    import torch
+    from paper_1910_02639_gb300.batch import DeviceSets, list_checksum
+    sets = wl.batched_sets(8, seed=516, nmin=500, nmax=20_000)
+    ds = DeviceSets(sets, "cuda:0", NGMAX)
+    ds.run_plain()
+    torch.cuda.synchronize()
+    ref = [ds.results(i) for i in range(len(sets))]
+    c_ref = list_checksum(ds.nb, ds.cnt, NGMAX)
+    ds.run_batched()
+    torch.cuda.synchronize()
+    for i in range(len(sets)):
+        nb, cnt, rho = ds.results(i)
+        k = np.minimum(cnt, NGMAX)
+        used = np.arange(NGMAX)[None, :] < k[:, None]
+        assert np.array_equal(cnt, ref[i][1])
+        assert np.array_equal(np.where(used, nb, -1), np.where(used, ref[i][0], -1))
+        assert np.array_equal(rho.view(np.int32), ref[i][2].view(np.int32))
+    assert list_checksum(ds.nb, ds.cnt, NGMAX) == c_ref
+    ds.free()
+
+
+def test_autotuner_table_and_params(bt):
+    from paper_1910_02639_gb300.autotune import Tuner, size_class
+    sets = wl.batched_sets(6, seed=517, nmin=2_000, nmax=50_000)
+    tu = Tuner("cuda:0", NGMAX, reps=1, sample_particles=100_000)
+    table = tu.tune(sets)
+    assert set(table) == {size_class(s.n) for s in sets}
+    for e in table.values():
+        assert e["bucket_size"] in (8, 16, 32, 64) and e["beta"] in (0.25, 0.5, 0.75)
+        assert e["group_size"] in (16, 32) and e["ms"] > 0
+    params = tu.params_for(sets)
+    _, _, ref = run_batched(bt, sets)
+    _, _, got = run_batched(bt, sets, params)
+    for i in range(len(sets)):
+        _assert_same(got[i], ref[i], "set %d tuned" % i)

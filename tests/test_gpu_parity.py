@@ -179,6 +179,42 @@ def test_large_h_windowed_path(bt, gpu, oracle):
     assert rel.max() < DENS_TOL
 
 
+def test_windowed_path_on_a_large_set(bt, gpu, oracle):
+    """Work units whose candidates span several windows but only a small part
+    of a large set take the windowed path (not the scan)."""
+    s = wl.uniform_cube(150_000, seed=66, target=1500)
+    r = gpu.run_gpu(s, bucket_size=16, ngmax=300, density=True)
+    ot = oracle.OracleTree(s.x, s.y, s.z, bucket_size=16)
+    ref_nb, ref_cnt = ot.find(s.h, 300)
+    _assert_lists(r, ref_nb, ref_cnt)
+    assert ref_cnt.max() > 1024
+    rel = np.abs(r["rho"] - ot.density(s.h, s.m)) / ot.density(s.h, s.m)
+    assert rel.max() < DENS_TOL
+
+
+def test_huge_h_scan_mode(bt, gpu, oracle):
+    """A few particles whose 2h covers most of the set (the outskirts of a
+    Plummer sphere with analytic h): their work units scan the set in index
+    order.  Lists, counts and densities as the definition."""
+    base = wl.uniform_cube(20_000, seed=67, target=60)
+    h = base.h.copy()
+    rng = np.random.default_rng(67)
+    far = rng.choice(base.n, 200, replace=False)
+    h[far] = rng.uniform(0.2, 0.9, far.size).astype(np.float32)
+    # and one tight cluster of large-h particles, so whole work units are wide
+    x, y, z = base.x.copy(), base.y.copy(), base.z.copy()
+    x[:64], y[:64], z[:64] = 0.9 + 1e-3 * rng.random((3, 64)).astype(np.float32)
+    h[:64] = 0.45
+    s = wl._pack(x, y, z, h)
+    r = gpu.run_gpu(s, bucket_size=16, ngmax=512, density=True)
+    ref_nb, ref_cnt = _brute(oracle, s, 512)
+    _assert_lists(r, ref_nb, ref_cnt)
+    assert ref_cnt.max() > 5000
+    ot = oracle.OracleTree(s.x, s.y, s.z, bucket_size=16)
+    rel = np.abs(r["rho"] - ot.density(s.h, s.m)) / ot.density(s.h, s.m)
+    assert rel.max() < DENS_TOL
+
+
 def test_boundary_pairs_exact_predicate(bt, gpu, oracle):
     """Pairs placed at D = R within a few ulps: the FP32 filter must defer to
     the binary64 predicate."""
