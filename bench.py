@@ -270,6 +270,10 @@ def run_gpu(args):
     if not args.no_batched:
         out["batched"] = run_batched_section(args, bt, dev, stream, dist, rank, ws)
 
+    # ---- serving: Poisson request stream, continuous batching vs plain
+    if not args.no_serving:
+        out["serving"] = run_serving_section(args, dev, rank, ws)
+
     # ---- end to end through the public API, host buffers
     if not args.no_e2e:
         out["e2e"] = run_e2e(args, bt, s, cfg, dev, stream, dist, ws, pairs)
@@ -401,6 +405,68 @@ def run_batched_section(args, bt, dev, stream, dist, rank, ws):
             "steps": K, "warmup": 3}
 
 
+# ---------------------------------------------------------------- serving
+def run_serving_section(args, dev, rank, ws):
+    """Poisson arrivals (200 requests/s), sizes log-uniform in [1e4, 2e6], the
+    three distributions of the batched workload; each request = copy in +
+    build + find + density, results left in HBM.  Served by the
+    continuous-batching loop (4 slots) and, under the same arrivals, by the
+    plain path one job at a time.  Then the same requests all at once
+    (saturated) for throughput.  Each rank serves its own share of the
+    stream."""
+    import numpy as np
+    import torch
+    from paper_1910_02639_gb300 import serving
+    from paper_1910_02639_gb300 import workloads as wl
+    from paper_1910_02639_gb300.batch import list_checksum, shard_sets
+    specs = wl.request_stream(args.serving_requests, seed=1915, rate=200.0)
+    mine = shard_sets([1] * len(specs), ws)[rank]  # round-robin by arrival
+    ngmax = 256
+    reqs = [serving.make_request(i, specs[i][0], wl.make_set(*specs[i][1:])) for i in mine]
+    sums, pairs = {}, {}
+
+    def grab(tag):
+        def f(res):
+            c = int(res.cnt.to(torch.int64).sum().item())
+            rb = int(res.rho.view(torch.int32).to(torch.int64).sum().item())
+            sums[(tag, res.rid)] = (c, list_checksum(res.nb, res.cnt, ngmax), rb)
+            pairs[res.rid] = c
+        return f
+
+    # warm-up (kernels, allocator, trees)
+    srv = serving.Server(dev, ngmax=ngmax, slots=args.serving_slots)
+    try:
+        serving.replay(srv, [serving.make_request(-1, 0.0, wl.make_set("uniform_cube", 50_000, 1, 100.0))])
+        served = serving.replay(srv, reqs, on_result=grab("served"))
+        for r in reqs:
+            r.arrival = 0.0
+        sat = serving.replay(srv, reqs)
+    finally:
+        srv.close()
+    for r, sp in zip(reqs, (specs[i] for i in mine)):
+        r.arrival = sp[0]
+    serving.replay_plain([serving.make_request(-1, 0.0, wl.make_set("uniform_cube", 50_000, 1, 100.0))],
+                         dev, ngmax)
+    plain = serving.replay_plain(reqs, dev, ngmax, on_result=grab("plain"))
+    for r in reqs:
+        r.arrival = 0.0
+    plain_sat = serving.replay_plain(reqs, dev, ngmax)
+    total = sum(pairs.values())
+    same = all(sums[("served", r.rid)] == sums[("plain", r.rid)] for r in reqs)
+    st = serving.latency_stats(served, total)
+    sp_ = serving.latency_stats(plain, total)
+    out = {"workload": f"poisson_{args.serving_requests}_requests_200_per_s",
+           "requests": len(reqs), "particles": int(sum(r.n for r in reqs)), "pairs": total,
+           "slots": args.serving_slots, "ngmax": ngmax,
+           "served": {k: st[k] for k in ("p50_ms", "p99_ms", "mean_ms", "pairs_per_s")},
+           "plain": {k: sp_[k] for k in ("p50_ms", "p99_ms", "mean_ms", "pairs_per_s")},
+           "saturated_pairs_per_s": {"served": serving.latency_stats(sat, total)["pairs_per_s"],
+                                     "plain": serving.latency_stats(plain_sat, total)["pairs_per_s"]},
+           "mean_batch_size": float(np.mean([r.batch_size for r in served])),
+           "identical_to_plain": bool(same)}
+    return out
+
+
 # ---------------------------------------------------------------- CPU oracle
 def cpu_baseline(s, cfg, sample):
     """The oracle as it stands: BuildTree over the whole set, FindNeighbors for
@@ -479,6 +545,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-sets", type=int, default=256)
     ap.add_argument("--batched-steps", type=int, default=5)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=200)
+    ap.add_argument("--serving-slots", type=int, default=4)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
