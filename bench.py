@@ -237,9 +237,37 @@ def run_gpu(args):
     barrier(dist, dev)
     t1 = time.time()
     launches = bt.btree_kernel_launches() - l0
+    step_ms = e0.elapsed_time(e1) / K
+
+    # ---- the same step as one CUDA graph (btree_build_find_batched, one set)
+    gtree = None
+    off = [0, n]
+    t_cap = time.perf_counter()
+    gtree = bt.btree_build_find_batched(x, y, z, h, off, ngmax, nb, cnt, m=m, rho=rho,
+                                        params=dict(bucket_size=sb, alpha=cfg["alpha"], beta=cfg["beta"]),
+                                        stream=stream, tree=gtree)
+    capture_ms = (time.perf_counter() - t_cap) * 1e3
+    for _ in range(2):
+        gtree = bt.btree_build_find_batched(x, y, z, h, off, ngmax, nb, cnt, m=m, rho=rho,
+                                            params=dict(bucket_size=sb, alpha=cfg["alpha"],
+                                                        beta=cfg["beta"]), stream=stream, tree=gtree)
+    g0 = bt.btree_kernel_launches()
+    barrier(dist, dev)
+    t0g = time.time()
+    e0.record(stream)
+    for k in range(K):
+        gtree = bt.btree_build_find_batched(x, y, z, h, off, ngmax, nb, cnt, m=m, rho=rho,
+                                            params=dict(bucket_size=sb, alpha=cfg["alpha"],
+                                                        beta=cfg["beta"]), stream=stream, tree=gtree)
+    e1.record(stream)
+    barrier(dist, dev)
+    t1g = time.time()
+    graph_launches = bt.btree_kernel_launches() - g0
+    graph_ms = e0.elapsed_time(e1) / K
+    graph_pairs = int(cnt.to(torch.int64).sum().item())
+    gtree.free()
     time.sleep(0.2)
     sampler.stop()
-    step_ms = e0.elapsed_time(e1) / K
     find_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(f0, f1))
     step_ms_max = reduce_max(dist, step_ms, dev)
     value = pairs * ws / (step_ms_max * 1e-3)
@@ -264,7 +292,13 @@ def run_gpu(args):
            "build_ms": round(statistics.mean(build_ms), 4), "find_ms": round(find_ms, 4),
            "roofline": roofline, "step_roofline": step_roofline,
            "gpu_launches": int(launches),
-           "clocks": sampler.summary(t0, t1)}
+           "graph_form": {"ms_per_step": reduce_max(dist, graph_ms, dev),
+                          "value": graph_pairs * ws / (reduce_max(dist, graph_ms, dev) * 1e-3),
+                          "gpu_launches": int(graph_launches), "first_call_ms": round(capture_ms, 3),
+                          "identical_pairs": graph_pairs == pairs,
+                          "form": "btree_build_find_batched: build+find+density as one CUDA graph "
+                                  "launch per step (device-side level and ratio loops)"},
+           "clocks": sampler.summary(t0, t1g)}
 
     # ---- many uneven sets: batched vs the plain per-set path
     if not args.no_batched:
@@ -377,13 +411,19 @@ def run_batched_section(args, bt, dev, stream, dist, rank, ws):
     tuned_ms = _timed(lambda: ds.run_batched(tuned, stream), stream, K)
     same_t = ((int(ds.cnt.to(torch.int64).sum().item()), list_checksum(ds.nb, ds.cnt, ngmax)) == ref
               and torch.equal(ds.rho, rho_ref))
+    l0 = bt.btree_kernel_launches()
+    graph_ms = _timed(lambda: ds.run_graph(tuned, stream), stream, K)
+    launches_graph = (bt.btree_kernel_launches() - l0) // (K + 3)
+    same_g = ((int(ds.cnt.to(torch.int64).sum().item()), list_checksum(ds.nb, ds.cnt, ngmax)) == ref
+              and torch.equal(ds.rho, rho_ref))
     pairs = ref[0]
     all_pairs = pairs
     if dist:
         t = torch.tensor([pairs], dtype=torch.float64, device=dev)
         dist.all_reduce(t)
         all_pairs = int(t.item())
-    plain_ms, batched_ms, tuned_ms = (reduce_max(dist, v, dev) for v in (plain_ms, batched_ms, tuned_ms))
+    plain_ms, batched_ms, tuned_ms, graph_ms = (reduce_max(dist, v, dev)
+                                                for v in (plain_ms, batched_ms, tuned_ms, graph_ms))
     ds.free()
     rate = lambda ms: all_pairs / (ms * 1e-3)
     table = {str(k): {kk: v[kk] for kk in ("bucket_size", "beta", "group_size")}
@@ -400,7 +440,13 @@ def run_batched_section(args, bt, dev, stream, dist, rank, ws):
             "tuned": {"value": rate(tuned_ms), "ms_per_step": tuned_ms,
                       "identical_to_plain": bool(same_t), "table": table,
                       "tuning_s": round(tune_s, 2), "trials": tuner.trials},
+            "graph": {"value": rate(graph_ms), "ms_per_step": graph_ms,
+                      "launches_per_step": int(launches_graph),
+                      "form": "btree_build_find_batched with the tuned parameters: one CUDA graph "
+                              "launch per step, level and ratio loops as device-side while-nodes",
+                      "identical_to_plain": bool(same_g)},
             "speedup_batched_vs_plain": plain_ms / batched_ms,
+            "speedup_graph_vs_plain": plain_ms / graph_ms,
             "speedup_tuned_vs_plain": plain_ms / tuned_ms,
             "steps": K, "warmup": 3}
 

@@ -153,6 +153,28 @@ int btree_build_batched(const float *x, const float *y, const float *z, const fl
                         const bt_allocator *alloc, void *stream, btree_t **out);
 
 /*
+ * btree_build_find_batched -- btree_build_batched followed by
+ * btree_find_neighbors_density (m != NULL) or btree_find_neighbors (m ==
+ * NULL), as ONE CUDA graph launch on `stream`.  Inside the graph the level
+ * loop of BuildTree and the ratio-test loop of Eq. 4 are conditional
+ * while-nodes whose conditions the level kernels set on the device, so the
+ * host never waits between steps.  Results are those of the separate calls.
+ * The captured graph is kept in the handle and relaunched without a new
+ * capture while every pointer and size stays the same (the per-set
+ * parameters may change).
+ * m, rho : device float32 [n] or both NULL (no density).
+ * Other arguments: as btree_build_batched and btree_find_neighbors_density.
+ * Synchronises `stream` before returning (the device reports capacity
+ * problems, and the call grows the handle's buffers and runs again).
+ * Returns BT_WARN_NGMAX when some row was capped, else as btree_build.
+ */
+int btree_build_find_batched(const float *x, const float *y, const float *z, const float *h,
+                             const float *m, const int64_t *offsets, int nsets,
+                             const bt_set_params *params, int ngmax, int32_t *neighbors,
+                             int32_t *counts, float *rho, const bt_allocator *alloc, void *stream,
+                             btree_t **out);
+
+/*
  * btree_find_neighbors -- FindNeighbors (Algorithm 2) for every particle.
  *
  * N(i) = { j != i : D(i,j) < (2 h_i)^2 } (strict, binary64, see above);

@@ -17,7 +17,8 @@ import os
 import threading
 
 __all__ = [
-    "BtreeError", "Tree", "btree_build", "btree_build_batched", "btree_find_neighbors",
+    "BtreeError", "Tree", "btree_build", "btree_build_batched", "btree_build_find_batched",
+    "btree_find_neighbors",
     "btree_find_neighbors_density", "btree_find_neighbors_density_noalloc",
     "btree_noalloc_max_particles", "sph_density", "btree_status", "btree_get_info",
     "btree_export", "btree_free", "btree_strerror", "btree_version", "btree_kernel_launches",
@@ -76,6 +77,10 @@ def _load():
         lib.btree_build_batched.restype = ctypes.c_int
         lib.btree_build_batched.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int, vp, vp, vp,
                                             ctypes.POINTER(vp)]
+        lib.btree_build_find_batched.restype = ctypes.c_int
+        lib.btree_build_find_batched.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int, vp,
+                                                 ctypes.c_int, vp, vp, vp, vp, vp,
+                                                 ctypes.POINTER(vp)]
         lib.btree_find_neighbors.restype = ctypes.c_int
         lib.btree_find_neighbors.argtypes = [vp, ctypes.c_int, vp, vp, vp]
         lib.btree_find_neighbors_density.restype = ctypes.c_int
@@ -184,6 +189,22 @@ class _SetParams(ctypes.Structure):
                 ("group_size", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
+def _set_params(params, nsets):
+    if params is None:
+        return None
+    plist = [params] * nsets if isinstance(params, dict) else list(params)
+    if len(plist) != nsets:
+        raise ValueError("one parameter dict per set")
+    c_par = (_SetParams * nsets)()
+    for i, p in enumerate(plist):
+        c_par[i].bucket_size = int(p.get("bucket_size", 16))
+        c_par[i].flags = BT_SET_OCTREE if p.get("octree", False) else 0
+        c_par[i].alpha = float(p.get("alpha", 0.5))
+        c_par[i].beta = float(p.get("beta", 0.5))
+        c_par[i].group_size = int(p.get("group_size", 0))
+    return c_par
+
+
 def btree_build_batched(x, y, z, h, offsets, params=None, stream=None,
                         tree: Tree | None = None) -> Tree:
     """BuildTree for many sets at once.  x, y, z, h: the sets concatenated;
@@ -199,20 +220,42 @@ def btree_build_batched(x, y, z, h, offsets, params=None, stream=None,
         raise ValueError("offsets must run from 0 to the number of particles")
     ptrs = [_dptr(a, torch.float32, nm, n) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (h, "h"))]
     c_offs = (ctypes.c_int64 * (nsets + 1))(*offs)
-    c_par = None
-    if params is not None:
-        plist = [params] * nsets if isinstance(params, dict) else list(params)
-        c_par = (_SetParams * nsets)()
-        for i, p in enumerate(plist):
-            c_par[i].bucket_size = int(p.get("bucket_size", 16))
-            c_par[i].flags = BT_SET_OCTREE if p.get("octree", False) else 0
-            c_par[i].alpha = float(p.get("alpha", 0.5))
-            c_par[i].beta = float(p.get("beta", 0.5))
-            c_par[i].group_size = int(p.get("group_size", 0))
+    c_par = _set_params(params, nsets)
     t = tree if tree is not None else Tree()
     st = lib.btree_build_batched(*ptrs, c_offs, nsets, c_par, None,
                                  ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(t._ptr))
     _check(st, "btree_build_batched")
+    t.status = st
+    t.n = n
+    return t
+
+
+def btree_build_find_batched(x, y, z, h, offsets, ngmax: int, neighbors, counts, m=None, rho=None,
+                             params=None, stream=None, tree: Tree | None = None) -> Tree:
+    """Batched build + find (+ density when m and rho are given) as one CUDA
+    graph launch; synchronous.  Arguments as btree_build_batched and
+    btree_find_neighbors_density."""
+    import torch
+    lib = _load()
+    n = int(x.numel())
+    offs = [int(v) for v in offsets]
+    nsets = len(offs) - 1
+    if nsets < 1 or offs[0] != 0 or offs[-1] != n:
+        raise ValueError("offsets must run from 0 to the number of particles")
+    ptrs = [_dptr(a, torch.float32, nm, n) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (h, "h"))]
+    if (m is None) != (rho is None):
+        raise ValueError("give both m and rho, or neither")
+    pm = _dptr(m, torch.float32, "m", n) if m is not None else None
+    prho = _dptr(rho, torch.float32, "rho", n) if rho is not None else None
+    pnb = _dptr(neighbors, torch.int32, "neighbors", n * ngmax)
+    pc = _dptr(counts, torch.int32, "counts", n)
+    c_offs = (ctypes.c_int64 * (nsets + 1))(*offs)
+    c_par = _set_params(params, nsets)
+    t = tree if tree is not None else Tree()
+    st = lib.btree_build_find_batched(*ptrs, pm, c_offs, nsets, c_par, int(ngmax), pnb, pc, prho,
+                                      None, ctypes.c_void_p(_stream_ptr(stream)),
+                                      ctypes.byref(t._ptr))
+    _check(st, "btree_build_find_batched")
     t.status = st
     t.n = n
     return t

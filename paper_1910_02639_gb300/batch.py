@@ -6,6 +6,8 @@ It can run them two ways, with identical results:
 
 * ``run_batched`` -- one ``btree_build_batched`` over all sets, then one fused
   find + density call (a few launches for the whole batch);
+* ``run_graph`` -- the same two steps as one CUDA graph launch
+  (``btree_build_find_batched``);
 * ``run_plain`` -- the plain path: ``btree_build`` and the fused find for each
   set in turn, each set on its own tree.
 
@@ -16,7 +18,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import (btree_build, btree_build_batched, btree_find_neighbors_density)
+from . import (btree_build, btree_build_batched, btree_build_find_batched,
+               btree_find_neighbors_density)
 
 DEFAULT_PARAMS = dict(bucket_size=16, alpha=0.5, beta=0.5, octree=False, group_size=0)
 
@@ -65,6 +68,14 @@ class DeviceSets:
                                          self.params_list(params), stream=stream, tree=self._tree)
         btree_find_neighbors_density(self._tree, self.m, self.ngmax, self.nb, self.cnt, self.rho,
                                      stream=stream)
+        return self._tree
+
+    def run_graph(self, params=None, stream=None):
+        """The batched build and the fused find as one CUDA graph launch."""
+        self._tree = btree_build_find_batched(self.x, self.y, self.z, self.h, self.offsets,
+                                              self.ngmax, self.nb, self.cnt, m=self.m, rho=self.rho,
+                                              params=self.params_list(params), stream=stream,
+                                              tree=self._tree)
         return self._tree
 
     def run_plain(self, params=None, stream=None):

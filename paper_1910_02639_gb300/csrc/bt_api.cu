@@ -15,8 +15,24 @@ using namespace bt;
 
 namespace bt {
 static std::atomic<uint64_t> g_launches{0};
-void note_launch(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+// Launches issued while capturing a graph are counted when the graph runs.
+static thread_local bool g_capturing = false;
+void note_launch(int k)
+{
+    if (!g_capturing) g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed);
+}
 }  // namespace bt
+
+// Everything a captured graph bakes in; an unchanged key relaunches it.
+struct GraphKey {
+    TreeDev T;
+    LevelBufs L;
+    const float *m;
+    float *smass, *rho;
+    int32_t *nbrs, *counts;
+    int ngmax, sms;
+};
+
 
 struct btree {
     int64_t n = 0;
@@ -59,6 +75,11 @@ struct btree {
     int ngroups = 0;
     bt_info info{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int64_t hist_need_seen = 0;  // largest level histogram asked for so far
+    // graph form: private capture streams, the executable graph and its key
+    cudaStream_t gs[3] = {nullptr, nullptr, nullptr};
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey{};
 };
 
 namespace {
@@ -205,13 +226,21 @@ int ensure_particle_caps(btree *t, int64_t n)
     return BT_OK;
 }
 
-int ensure_hist(btree *t, int64_t need)
+// Histogram capacity.  A big cell of c > kSmallCap particles has
+// b0^3 < max(8, 3.375 c/s) histogram entries (b0 >= 3 means cbrt(c/s) > 2,
+// so b0 < cbrt(c/s) + 1 < 1.5 cbrt(c/s)), and a level's cells are disjoint:
+// one level never needs more than n max(8/257, 3.375/s_min) entries.
+int ensure_hist(btree *t)
 {
+    const double per = std::max(8.0 / (double)(kSmallCap + 1), 3.375 / (double)t->s);
+    const int64_t need = std::max<int64_t>((int64_t)std::ceil((double)t->n * per) + 64,
+                                           t->hist_need_seen);
     if (t->cap_hist >= need) return BT_OK;
     int64_t c = std::max<int64_t>(need, 4096);
+    if (c >= INT32_MAX) return BT_ERR_CAPACITY;
     if (!realloc_dev(t, t->hist, 0, c, false) || !realloc_dev(t, t->hoff, 0, c, false) ||
         !realloc_dev(t, t->cursor, 0, c, false) ||
-        !realloc_dev(t, t->tiles, 0, scan_tile_count((int)c) + 1, false))
+        !realloc_dev(t, t->tiles, 0, scan_tile_count(c) + 1, false))
         return BT_ERR_OOM;
     t->cap_hist = c;
     return BT_OK;
@@ -238,97 +267,77 @@ int ensure_set_caps(btree *t, int nsets)
     return BT_OK;
 }
 
-int read_counters(btree *t)
+int read_counters(btree *t, cudaStream_t st)
 {
-    cudaMemcpyAsync(t->hctr, t->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, t->st);
-    cudaError_t e = cudaStreamSynchronize(t->st);
+    cudaMemcpyAsync(t->hctr, t->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return to_status(e);
     return to_status(cudaGetLastError());
 }
 
-constexpr int kRetry = 100;
-
-int do_build(btree *t, const float *x, const float *y, const float *z, const float *h)
+LevelBufs lview(const btree *t, const float *x, const float *y, const float *z, const float *h)
 {
-    const int ns = t->nsets;
-    cudaStream_t st = t->st;
-    TreeDev T = view(t);
-    // per-set tables (staged on the host by the caller)
-    cudaMemcpyAsync(t->set_rec, t->h_rec, sizeof(SetRec) * (size_t)ns, cudaMemcpyHostToDevice, st);
-    launch_init_counters(t->ctr, st);
-    launch_set_int(&t->ctr->nnodes, ns, st);  // nodes 0..ns-1 are the roots
-    launch_init_sets(T, t->set_rec, t->set_start, t->set_s, t->set_na, t->set_beta, t->set_gmax, st);
-    cudaEventRecord(t->ev0, st);
-    launch_bbox(T, x, y, z, h, t->sms, st);
-    launch_root_sets(T, t->big_ids[0], t->small, st);
-    launch_copy_leaf_roots(T, x, y, z, h, t->sms, st);
-    int rc = read_counters(t);
-    if (rc != BT_OK) return rc;
-    if (t->hctr->status & kStNonfinite) return BT_ERR_NONFINITE;
-    if (t->hctr->status & kStCapSmall) return kRetry;
-
-    {
-        Src in{x, y, z, h, nullptr, nullptr};
-        Src src = in;
-        int nb = t->hctr->nbig_next;
-        int cur = 0, dst = 0;
-        int64_t nslots = 0;
-        while (nb > 0) {
-            launch_big_setup(T, t->big, t->big_ids[cur], nb, st);
-            if ((rc = read_counters(t)) != BT_OK) return rc;
-            if (t->hctr->status & kStCapBig) return BT_ERR_CAPACITY;
-            const int hist_total = t->hctr->hist_total;
-            const int chunks = t->hctr->chunk_total;
-            if ((rc = ensure_hist(t, hist_total)) != BT_OK) return rc;
-            if (nslots + hist_total > t->cap_slots) {
-                int64_t c = std::max<int64_t>((int64_t)t->cap_slots * 2, nslots + hist_total + 4096);
-                if (c > INT32_MAX / 2) return BT_ERR_CAPACITY;
-                if (!realloc_dev(t, t->slots, nslots, c, true)) return BT_ERR_OOM;
-                t->cap_slots = (int)c;
-                T = view(t);
-            }
-            cudaMemsetAsync(t->hist, 0, sizeof(int) * (size_t)hist_total, st);
-            for (int it = 0; it < 16; it++) {
-                launch_set_int(&t->ctr->again, 0, st);
-                launch_big_hist(T, t->big, nb, chunks, src, t->hist, t->sms, st);
-                launch_big_ratio(T, t->big, nb, t->hist, hist_total, t->sms, st);
-                if ((rc = read_counters(t)) != BT_OK) return rc;
-                if (!t->hctr->again) break;
-                launch_big_zero(t->big, nb, t->hist, hist_total, t->sms, st);
-            }
-            launch_big_finish(T, t->big, nb, (int)nslots, st);
-            nslots += hist_total;
-            launch_set_int(&t->ctr->nslots, (int)nslots, st);
-            launch_scan(t->hist, hist_total, t->tiles, t->hoff, st);
-            launch_set_int(&t->ctr->nbig_next, 0, st);
-            launch_big_emit(T, t->big, nb, hist_total, t->hist, t->hoff, t->cursor, dst,
-                            t->big_ids[cur ^ 1], t->small, t->sms, st);
-            launch_big_scatter(T, t->big, nb, chunks, src, t->cursor, t->wpos[dst], t->wh[dst],
-                               t->sms, st);
-            if ((rc = read_counters(t)) != BT_OK) return rc;
-            if (t->hctr->status & (kStCapNodes | kStCapSlots | kStCapGroups | kStCapSmall)) return kRetry;
-            nb = t->hctr->nbig_next;
-            if (nb > t->cap_big) return BT_ERR_CAPACITY;
-            cur ^= 1;
-            src = Src{nullptr, nullptr, nullptr, nullptr, t->wpos[dst], t->wh[dst]};
-            dst ^= 1;
-        }
-        if ((rc = read_counters(t)) != BT_OK) return rc;
-        const int nsmall = t->hctr->nsmall;
-        Src s0{nullptr, nullptr, nullptr, nullptr, t->wpos[0], t->wh[0]};
-        Src s1{nullptr, nullptr, nullptr, nullptr, t->wpos[1], t->wh[1]};
-        launch_small(T, t->small, std::min(nsmall, t->cap_small), s0, s1, in, t->sms, st);
+    LevelBufs L;
+    L.in = Src{x, y, z, h, nullptr, nullptr};
+    for (int k = 0; k < 2; k++) {
+        L.wpos[k] = t->wpos[k];
+        L.wh[k] = t->wh[k];
+        L.ids[k] = t->big_ids[k];
     }
-    cudaEventRecord(t->ev1, st);
-    if ((rc = read_counters(t)) != BT_OK) return rc;
+    L.big = t->big;
+    L.hist = t->hist;
+    L.hoff = t->hoff;
+    L.cursor = t->cursor;
+    L.tiles = t->tiles;
+    L.small = t->small;
+    L.cap_hist = t->cap_hist;
+    L.cap_big = t->cap_big;
+    L.cap_tiles = scan_tile_count(t->cap_hist);
+    return L;
+}
+
+constexpr int kRetry = 100;
+constexpr unsigned kCapBits = kStCapNodes | kStCapSlots | kStCapGroups | kStCapSmall | kStCapBig;
+
+// Timing events: inside a capture an ordinary record only orders streams of
+// the capture; an external record is a real node of the graph.
+void record_event(cudaEvent_t ev, cudaStream_t st, bool capture)
+{
+    if (capture) cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+    else cudaEventRecord(ev, st);
+}
+
+// The steps before the level loop (both forms of the build).
+void launch_build_head(btree *t, const TreeDev &T, const LevelBufs &L, cudaStream_t st,
+                       bool capture = false)
+{
+    cudaMemcpyAsync(t->set_rec, t->h_rec, sizeof(SetRec) * (size_t)t->nsets, cudaMemcpyHostToDevice, st);
+    launch_init_counters(t->ctr, t->nsets, st);
+    launch_init_sets(T, t->set_rec, t->set_start, t->set_s, t->set_na, t->set_beta, t->set_gmax, st);
+    record_event(t->ev0, st, capture);
+    launch_bbox(T, L.in.x, L.in.y, L.in.z, L.in.h, t->sms, st);
+    launch_roots(T, L, t->sms, st);
+}
+
+// After the build (counters on the host): retry on capacity, info.
+int finish_build(btree *t, cudaStream_t st)
+{
     const Counters &c = *t->hctr;
-    if (c.status & (kStCapNodes | kStCapSlots | kStCapGroups | kStCapSmall)) return kRetry;
+    if (c.status & kStNonfinite) return BT_ERR_NONFINITE;
+    if (c.abort || (c.status & kCapBits)) {
+        t->hist_need_seen = std::max<int64_t>(t->hist_need_seen, c.hist_need);
+        return kRetry;
+    }
     t->ngroups = c.ngroups;
     NodeWalk w0;
-    cudaMemcpyAsync(&w0, t->walk, sizeof(NodeWalk), cudaMemcpyDeviceToHost, st);
+    w0.b = 0;
+    if (t->nsets > 0) cudaMemcpyAsync(&w0, t->walk, sizeof(NodeWalk), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return BT_ERR_CUDA;
     float ms = 0.0f;
-    cudaEventElapsedTime(&ms, t->ev0, t->ev1);
+    if (cudaEventElapsedTime(&ms, t->ev0, t->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        ms = 0.0f;
+    }
     bt_info &I = t->info;
     I.n = t->n;
     I.bucket_size = t->s;
@@ -342,19 +351,206 @@ int do_build(btree *t, const float *x, const float *y, const float *z, const flo
     return (c.status & kStOversized) ? BT_WARN_OVERSIZED_LEAF : BT_OK;
 }
 
+// Host-driven BuildTree: the host reads the device counters after each step
+// of the level loop and of the ratio loop (Eq. 4) to decide what follows.
+int do_build(btree *t, const float *x, const float *y, const float *z, const float *h)
+{
+    cudaStream_t st = t->st;
+    const TreeDev T = view(t);
+    const LevelBufs L = lview(t, x, y, z, h);
+    launch_build_head(t, T, L, st);
+    launch_level_go(t->ctr, 0, 0, 0, st);
+    int rc = read_counters(t, st);
+    if (rc != BT_OK) return rc;
+    if (t->hctr->status & kStNonfinite) return BT_ERR_NONFINITE;
+    while (t->hctr->level_go) {
+        LevelHints H{t->hctr->nbig_next, 0, 0};
+        launch_level_start(T, L, H, t->sms, 0, 0, st);
+        if ((rc = read_counters(t, st)) != BT_OK) return rc;
+        if (t->hctr->abort) break;
+        H.hist = t->hctr->hist_total;
+        H.chunks = t->hctr->chunk_total;
+        launch_level_zero(T, L, H, t->sms, st);
+        do {
+            launch_ratio_pass(T, L, H, t->sms, 0, 0, st);
+            if ((rc = read_counters(t, st)) != BT_OK) return rc;
+        } while (t->hctr->ratio_go);
+        launch_level_finish(T, L, H, t->sms, 0, 0, st);
+        if ((rc = read_counters(t, st)) != BT_OK) return rc;
+    }
+    if (!t->hctr->abort) launch_small(T, L, std::min(t->hctr->nsmall, t->cap_small), t->sms, st);
+    cudaEventRecord(t->ev1, st);
+    if ((rc = read_counters(t, st)) != BT_OK) return rc;
+    return finish_build(t, st);
+}
+
+// ---------------------------------------------------------------- graph form
+// A conditional while-node after the work captured so far on `st`; returns
+// its body graph.  Later work on `st` follows the node.
+cudaError_t add_while(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraph_t *body)
+{
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, deps, ed, nd, &p);
+    if (e != cudaSuccess) return e;
+    *body = p.conditional.phGraph_out[0];
+    return cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+cudaError_t capture_graph_of(cudaStream_t st, cudaGraph_t *g)
+{
+    cudaStreamCaptureStatus cs;
+    return cudaStreamGetCaptureInfo(st, &cs, nullptr, g, nullptr, nullptr, nullptr);
+}
+
+
+// Captures build + find (+ density) on the handle's private streams.  The
+// level loop and the ratio loop are while-nodes whose conditions the level
+// kernels set on the device.
+cudaError_t capture_step(btree *t, const GraphKey &K, cudaGraph_t *out)
+{
+    cudaStream_t s0 = t->gs[0], s1 = t->gs[1], s2 = t->gs[2];
+    const TreeDev &T = K.T;
+    const LevelBufs &L = K.L;
+    const LevelHints Hc{t->cap_big, t->cap_hist, t->n / kBigChunk + t->cap_big + 1};
+    cudaError_t e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t err = cudaSuccess;
+    auto chk = [&](cudaError_t x) { if (err == cudaSuccess && x != cudaSuccess) err = x; };
+    cudaGraph_t g0 = nullptr, lbody = nullptr, rbody = nullptr;
+    cudaGraphConditionalHandle hlevel = 0, hratio = 0;
+    launch_build_head(t, T, L, s0, true);
+    chk(capture_graph_of(s0, &g0));
+    if (err == cudaSuccess) chk(cudaGraphConditionalHandleCreate(&hlevel, g0, 0, cudaGraphCondAssignDefault));
+    launch_level_go(t->ctr, 0, hlevel, 1, s0);
+    if (err == cudaSuccess) chk(add_while(s0, hlevel, &lbody));
+    if (err == cudaSuccess) {
+        chk(cudaStreamBeginCaptureToGraph(s1, lbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        if (err == cudaSuccess) {
+            chk(cudaGraphConditionalHandleCreate(&hratio, lbody, 0, cudaGraphCondAssignDefault));
+            launch_level_start(T, L, Hc, t->sms, hratio, 1, s1);
+            launch_level_zero(T, L, Hc, t->sms, s1);
+            if (err == cudaSuccess) chk(add_while(s1, hratio, &rbody));
+            if (err == cudaSuccess) {
+                chk(cudaStreamBeginCaptureToGraph(s2, rbody, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal));
+                if (err == cudaSuccess) {
+                    launch_ratio_pass(T, L, Hc, t->sms, hratio, 1, s2);
+                    chk(cudaStreamEndCapture(s2, &rbody));
+                }
+            }
+            launch_level_finish(T, L, Hc, t->sms, hlevel, 1, s1);
+            chk(cudaStreamEndCapture(s1, &lbody));
+        }
+    }
+    launch_small(T, L, t->cap_small, t->sms, s0);
+    record_event(t->ev1, s0, true);
+    if (K.nbrs) chk(launch_find(T, -1, K.ngmax, K.nbrs, K.counts, K.m, K.smass, K.rho, t->sms, s0));
+    cudaGraph_t g = nullptr;
+    chk(cudaStreamEndCapture(s0, &g));
+    if (err != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return err;
+    }
+    *out = g;
+    return cudaSuccess;
+}
+
+// Kernels one run of the captured graph launched (for the launch counter).
+uint64_t graph_launches(const Counters &c, bool find, bool dens)
+{
+    // head: init_counters, init_sets, bbox, root_sets, copy_leaf_roots, level_go;
+    // per level: begin, setup, scan, zero, finish, 3 scans, emit, scatter, level_go;
+    // per ratio pass: hist, count, decide, zero, ratio_end; then small and find
+    return 6 + 11 * (uint64_t)c.level + 5 * (uint64_t)c.ratio_total + 1 + (find ? 1 + (dens ? 1 : 0) : 0);
+}
+
+int run_graph_step(btree *t, const float *x, const float *y, const float *z, const float *h,
+                   const float *m, int ngmax, int32_t *nbrs, int32_t *counts, float *rho,
+                   cudaStream_t user)
+{
+    for (int k = 0; k < 3; k++)
+        if (!t->gs[k] && cudaStreamCreateWithFlags(&t->gs[k], cudaStreamNonBlocking) != cudaSuccess)
+            return BT_ERR_CUDA;
+    GraphKey K;
+    std::memset(&K, 0, sizeof(K));
+    K.T = view(t);
+    K.L = lview(t, x, y, z, h);
+    K.m = m;
+    K.smass = m ? t->smass : nullptr;
+    K.rho = rho;
+    K.nbrs = nbrs;
+    K.counts = counts;
+    K.ngmax = ngmax;
+    K.sms = t->sms;
+    if (!t->gexec || std::memcmp(&K, &t->gkey, sizeof(GraphKey)) != 0) {
+        cudaGraph_t g = nullptr;
+        g_capturing = true;
+        cudaError_t e = capture_step(t, K, &g);
+        g_capturing = false;
+        if (e != cudaSuccess) return to_status(e);
+        bool updated = false;
+        if (t->gexec) {
+            cudaGraphExecUpdateResultInfo info;
+            updated = cudaGraphExecUpdate(t->gexec, g, &info) == cudaSuccess;
+            if (!updated) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(t->gexec);
+                t->gexec = nullptr;
+            }
+        }
+        if (!updated) e = cudaGraphInstantiate(&t->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            t->gexec = nullptr;
+            return to_status(e);
+        }
+        std::memcpy(&t->gkey, &K, sizeof(GraphKey));
+    }
+    // the graph runs on the private stream s0's ordering inside; it is
+    // launched on the caller's stream
+    cudaError_t e = cudaGraphLaunch(t->gexec, user);
+    if (e != cudaSuccess) return to_status(e);
+    int rc = read_counters(t, user);
+    if (rc != BT_OK) return rc;
+    note_launch((int)graph_launches(*t->hctr, nbrs != nullptr, m != nullptr));
+    return finish_build(t, user);
+}
+
 bool is_finite_d(double v) { return std::isfinite(v); }
 
 }  // namespace
 
-// Shared front end of btree_build and btree_build_batched: the per-set
-// records must already be staged in t->h_rec.
-static int build_core(btree *t, const float *x, const float *y, const float *z, const float *h)
+// Shared front end of the builds: the per-set records must already be staged
+// in t->h_rec.  `graph`: build (+ find) as one CUDA graph.
+static int build_core(btree *t, const float *x, const float *y, const float *z, const float *h,
+                      bool graph = false, const float *m = nullptr, int ngmax = 0,
+                      int32_t *nbrs = nullptr, int32_t *counts = nullptr, float *rho = nullptr,
+                      cudaStream_t user = nullptr)
 {
     int rc = BT_OK;
     for (int attempt = 0; attempt < 6; attempt++) {
         rc = ensure_particle_caps(t, t->n);
+        if (rc == BT_OK) rc = ensure_hist(t);
+        if (rc == BT_OK && m && t->cap_smass < t->n) {
+            if (!realloc_dev(t, t->smass, 0, std::max<int64_t>(t->n, 1), false)) rc = BT_ERR_OOM;
+            else t->cap_smass = std::max<int64_t>(t->n, 1);
+        }
         if (rc != BT_OK) break;
-        rc = do_build(t, x, y, z, h);
+        rc = graph ? run_graph_step(t, x, y, z, h, m, ngmax, nbrs, counts, rho, user)
+                   : do_build(t, x, y, z, h);
         if (rc != kRetry) break;
         // grow the tree-size buffers and build again
         int64_t cn = std::min<int64_t>((int64_t)t->cap_nodes * 2, INT32_MAX / 2);
@@ -455,9 +651,9 @@ int btree_build(const float *x, const float *y, const float *z, const float *h, 
     return build_core(t, x, y, z, h);
 }
 
-int btree_build_batched(const float *x, const float *y, const float *z, const float *h,
-                        const int64_t *offsets, int nsets, const bt_set_params *params,
-                        const bt_allocator *alloc, void *stream, btree_t **out)
+static int stage_batched(const float *x, const float *y, const float *z, const float *h,
+                         const int64_t *offsets, int nsets, const bt_set_params *params,
+                         const bt_allocator *alloc, void *stream, btree_t **out, btree **tp)
 {
     if (!out || !offsets || nsets < 1 || nsets > (1 << 24)) return BT_ERR_ARG;
     if (offsets[0] != 0) return BT_ERR_ARG;
@@ -492,7 +688,39 @@ int btree_build_batched(const float *x, const float *y, const float *z, const fl
         const int g = params && params[i].group_size > 0 ? params[i].group_size : kGroupMax;
         stage_set(t, i, offsets[i], offsets[i + 1], s, a, b, f, g);
     }
+    *tp = t;
+    return BT_OK;
+}
+
+int btree_build_batched(const float *x, const float *y, const float *z, const float *h,
+                        const int64_t *offsets, int nsets, const bt_set_params *params,
+                        const bt_allocator *alloc, void *stream, btree_t **out)
+{
+    btree *t = nullptr;
+    int rc = stage_batched(x, y, z, h, offsets, nsets, params, alloc, stream, out, &t);
+    if (rc != BT_OK) return rc;
     return build_core(t, x, y, z, h);
+}
+
+int btree_build_find_batched(const float *x, const float *y, const float *z, const float *h,
+                             const float *m, const int64_t *offsets, int nsets,
+                             const bt_set_params *params, int ngmax, int32_t *neighbors,
+                             int32_t *counts, float *rho, const bt_allocator *alloc, void *stream,
+                             btree_t **out)
+{
+    if (ngmax < 1 || !offsets || nsets < 1) return BT_ERR_ARG;
+    if (offsets[nsets] > 0 && (!neighbors || !counts || (m && !rho))) return BT_ERR_ARG;
+    btree *t = nullptr;
+    int rc = stage_batched(x, y, z, h, offsets, nsets, params, alloc, stream, out, &t);
+    if (rc != BT_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool any = t->n > 0;
+    rc = build_core(t, x, y, z, h, true, any ? m : nullptr, ngmax, any ? neighbors : nullptr,
+                    counts, any && m ? rho : nullptr, st);
+    if (rc < 0 || !any) return rc;
+    const unsigned stw = t->hctr->status;
+    if (stw & kStNgmax) return BT_WARN_NGMAX;
+    return rc;
 }
 
 int btree_find_neighbors(const btree_t *t, int ngmax, int32_t *neighbors, int32_t *counts, void *stream)
@@ -637,6 +865,9 @@ int btree_export(const btree_t *t, void *stream, double *node_lo, double *node_h
 void btree_free(btree_t *t)
 {
     if (!t) return;
+    if (t->gexec) cudaGraphExecDestroy(t->gexec);
+    for (int k = 0; k < 3; k++)
+        if (t->gs[k]) cudaStreamDestroy(t->gs[k]);
     free_all(t);
     if (t->hctr) cudaFreeHost(t->hctr);
     if (t->h_rec) cudaFreeHost(t->h_rec);

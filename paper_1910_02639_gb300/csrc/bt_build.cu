@@ -142,7 +142,7 @@ __global__ void k_init_sets(TreeDev T, const SetRec *rec, int *set_start, int *s
 // leaf (work units now, particles copied by k_copy_leaf_roots), a set of
 // <= kSmallCap particles goes to the warp builder, a larger one to the big
 // levels.
-__device__ void root_set(TreeDev &T, int s, int *big_ids, SmallItem *small)
+__device__ void root_set(TreeDev &T, int s, const LevelBufs &L)
 {
     const int start = T.set_start[s], n = T.set_start[s + 1] - start;
     NodeGeom g;
@@ -168,23 +168,36 @@ __device__ void root_set(TreeDev &T, int s, int *big_ids, SmallItem *small)
         emit_groups(T, s, start, n);
     } else if (n <= kSmallCap) {
         const int k = atomicAdd(&T.ctr->nsmall, 1);
-        if (k < T.cap_small) small[k] = SmallItem{s, 2};
+        if (k < T.cap_small) L.small[k] = SmallItem{s, 2};
         else atomicOr(&T.ctr->status, kStCapSmall);
     } else {
-        big_ids[atomicAdd(&T.ctr->nbig_next, 1)] = s;
+        const int k = atomicAdd(&T.ctr->nbig_next, 1);
+        if (k < L.cap_big) {
+            L.ids[0][k] = s;
+        } else {
+            atomicOr(&T.ctr->status, kStCapBig);
+            T.ctr->abort = 1;
+        }
     }
 }
 
-__global__ void k_root_sets(TreeDev T, int *big_ids, SmallItem *small)
+// A build whose input failed the finiteness check stops here (the bounding
+// boxes, and so everything below, would be meaningless).
+__global__ void k_root_sets(TreeDev T, LevelBufs L)
 {
+    if (T.ctr->status & kStNonfinite) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) T.ctr->abort = 1;
+        return;
+    }
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < T.nsets; s += gridDim.x * blockDim.x)
-        root_set(T, s, big_ids, small);
+        root_set(T, s, L);
 }
 
 // Sets that are one leaf: their particles are final where they are.
 __global__ void k_copy_leaf_roots(TreeDev T, const float *__restrict__ x, const float *__restrict__ y,
                                   const float *__restrict__ z, const float *__restrict__ h)
 {
+    if (T.ctr->abort) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.n; i += gridDim.x * blockDim.x) {
         const int s = T.nsets == 1 ? 0 : find_set(T.set_start, T.nsets, i);
         if (!(T.set_flags[s] & kSetLeafRoot)) continue;
@@ -195,41 +208,81 @@ __global__ void k_copy_leaf_roots(TreeDev T, const float *__restrict__ x, const 
 }
 
 // ------------------------------------------------------------------ big cells
-__global__ void k_big_setup(TreeDev T, BigCell *big, const int *ids, int nb)
+// Every level kernel reads its work counts from the device counters, so the
+// same kernels run host-driven (the host reads the counters between steps)
+// or inside a CUDA graph whose loops are conditional nodes.
+
+// One thread: whether another level follows; sets the graph's loop condition.
+__global__ void k_level_go(Counters *ctr, int advance, cudaGraphConditionalHandle h, int graph)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
-    int node = ids[i];
-    const NodeGeom &g = T.geom[node];
-    int b0 = set_b0(T, g.set, g.count);
-    BigCell c;
-    c.node = node;
-    c.b0 = b0;
-    c.b = b0;
-    c.hist_base = b0 * b0 * b0;  // sizes, scanned next
-    c.chunk_base = (g.count + kBigChunk - 1) / kBigChunk;
-    c.state = 0;
-    c.slot0 = 0;
-    c.u = 0;
-    c.ne = 0;
-    c.lastj = -1;
-    c.halved = 0;
-    c.set = g.set;
-    c.w[0] = c.w[1] = c.w[2] = 0.0;
-    big[i] = c;
+    if (advance) ctr->level += 1;
+    const int go = ctr->nbig_next > 0 && !ctr->abort && ctr->level < kDepthMax;
+    ctr->level_go = go;
+    if (graph) cudaGraphSetConditional(h, go);
 }
 
-// One block: exclusive scans of hist sizes and chunk counts over nb cells.
-__global__ void __launch_bounds__(1024) k_big_scan(BigCell *big, int nb, Counters *ctr)
+// One thread: the cells queued by the previous level become this level's.
+__global__ void k_level_begin(Counters *ctr)
+{
+    ctr->nbig = ctr->nbig_next;
+    ctr->nbig_next = 0;
+    ctr->ratio_it = 0;
+    ctr->again = 0;
+}
+
+__global__ void k_big_setup(TreeDev T, LevelBufs L)
+{
+    const Counters *ctr = T.ctr;
+    if (ctr->abort) return;
+    const int nb = ctr->nbig;
+    const int *ids = L.ids[ctr->level & 1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x) {
+        const int node = ids[i];
+        const NodeGeom &g = T.geom[node];
+        const int b0 = set_b0(T, g.set, g.count);
+        BigCell c;
+        c.node = node;
+        c.b0 = b0;
+        c.b = b0;
+        c.hist_n = b0 * b0 * b0;
+        c.chunk_n = (g.count + kBigChunk - 1) / kBigChunk;
+        c.hist_base = 0;
+        c.chunk_base = 0;
+        c.state = 0;
+        c.slot0 = 0;
+        c.u = 0;
+        c.ne = 0;
+        c.lastj = -1;
+        c.halved = 0;
+        c.set = g.set;
+        c.w[0] = c.w[1] = c.w[2] = 0.0;
+        L.big[i] = c;
+    }
+}
+
+// One block: exclusive scans of histogram sizes and chunk counts over the
+// level's cells; reserves the level's sub-cells; capacity checks.
+__global__ void __launch_bounds__(1024) k_big_scan(TreeDev T, LevelBufs L,
+                                                   cudaGraphConditionalHandle hratio, int graph)
 {
     __shared__ long long sh_h[1024], sh_c[1024];
     __shared__ long long carry_h, carry_c;
+    Counters *ctr = T.ctr;
+    if (ctr->abort) {
+        if (threadIdx.x == 0) {
+            ctr->ratio_go = 0;
+            if (graph) cudaGraphSetConditional(hratio, 0);
+        }
+        return;
+    }
+    const int nb = ctr->nbig;
+    BigCell *big = L.big;
     if (threadIdx.x == 0) { carry_h = 0; carry_c = 0; }
     __syncthreads();
     for (int base = 0; base < nb; base += 1024) {
         int i = base + threadIdx.x;
-        long long vh = i < nb ? big[i].hist_base : 0;
-        long long vc = i < nb ? big[i].chunk_base : 0;
+        long long vh = i < nb ? big[i].hist_n : 0;
+        long long vc = i < nb ? big[i].chunk_n : 0;
         sh_h[threadIdx.x] = vh;
         sh_c[threadIdx.x] = vc;
         __syncthreads();
@@ -242,7 +295,8 @@ __global__ void __launch_bounds__(1024) k_big_scan(BigCell *big, int nb, Counter
             __syncthreads();
         }
         if (i < nb) {
-            big[i].hist_base = (int)(carry_h + sh_h[threadIdx.x] - vh);
+            const long long hb = carry_h + sh_h[threadIdx.x] - vh;
+            big[i].hist_base = (int)min(hb, (long long)INT_MAX);
             big[i].chunk_base = (int)(carry_c + sh_c[threadIdx.x] - vc);
         }
         __syncthreads();
@@ -253,10 +307,30 @@ __global__ void __launch_bounds__(1024) k_big_scan(BigCell *big, int nb, Counter
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        ctr->hist_total = (int)min(carry_h, (long long)INT_MAX);
-        ctr->chunk_total = (int)carry_c;
-        if (carry_h > INT_MAX) atomicOr(&ctr->status, kStCapBig);
+        const long long ht = carry_h;
+        const bool fit_hist = ht <= L.cap_hist && ht < INT_MAX;
+        const bool fit_slots = (long long)ctr->nslots + ht <= (long long)T.cap_slots;
+        const int ok = fit_hist && fit_slots;
+        ctr->hist_total = ok ? (int)ht : 0;
+        ctr->chunk_total = ok ? (int)carry_c : 0;
+        if (ok) {
+            ctr->slot_base = ctr->nslots;
+            ctr->nslots += (int)ht;
+        } else {
+            ctr->hist_need = ht;
+            atomicOr(&ctr->status, fit_hist ? kStCapSlots : kStCapBig);
+            ctr->abort = 1;
+        }
+        ctr->ratio_go = ok;
+        if (graph) cudaGraphSetConditional(hratio, ok);
     }
+}
+
+__global__ void __launch_bounds__(256) k_zero_hist(const Counters *ctr, int *hist)
+{
+    if (ctr->abort) return;
+    const int n = ctr->hist_total;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) hist[e] = 0;
 }
 
 __device__ __forceinline__ int find_cell_by_chunk(const BigCell *big, int nb, int chunk)
@@ -304,10 +378,15 @@ __device__ __forceinline__ int sub_cell_id(const float4 &p, const NodeWalk &w, c
 }
 
 // Histogram pass of one candidate b for every pending big cell.
-__global__ void __launch_bounds__(256) k_big_hist(TreeDev T, const BigCell *big, int nb,
-                                                  Src src, int *hist)
+__global__ void __launch_bounds__(256) k_big_hist(TreeDev T, LevelBufs L)
 {
-    const int total = T.ctr->chunk_total;
+    const Counters *ctr = T.ctr;
+    if (ctr->abort) return;
+    const int nb = ctr->nbig;
+    const int total = ctr->chunk_total;
+    const BigCell *big = L.big;
+    int *hist = L.hist;
+    const Src src = level_src(L, ctr->level);
     for (int chunk = blockIdx.x; chunk < total; chunk += gridDim.x) {
         int ci = find_cell_by_chunk(big, nb, chunk);
         BigCell c = big[ci];
@@ -327,9 +406,14 @@ __global__ void __launch_bounds__(256) k_big_hist(TreeDev T, const BigCell *big,
 
 // Per-cell statistics of the current histogram (Eq. 4 numerator, non-empty
 // sub-cells), accumulated over the whole level by all blocks.
-__global__ void __launch_bounds__(256) k_big_count(TreeDev T, BigCell *big, int nb, const int *hist,
-                                                   int total)
+__global__ void __launch_bounds__(256) k_big_count(TreeDev T, LevelBufs L)
 {
+    const Counters *ctr = T.ctr;
+    if (ctr->abort) return;
+    const int nb = ctr->nbig;
+    const int total = ctr->hist_total;
+    BigCell *big = L.big;
+    const int *hist = L.hist;
     for (int e0 = blockIdx.x * blockDim.x; e0 < total; e0 += gridDim.x * blockDim.x) {
         const int e = e0 + threadIdx.x;
         int ci = -1, u = 0, ne = 0, lj = -1;
@@ -370,11 +454,8 @@ __global__ void __launch_bounds__(256) k_big_count(TreeDev T, BigCell *big, int 
 }
 
 // Ratio test (Eq. 4), one thread per big cell: accept b or halve it.
-__global__ void k_big_decide(TreeDev T, BigCell *big, int nb)
+__device__ __forceinline__ void decide_cell(const TreeDev &T, BigCell &c)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
-    BigCell &c = big[i];
     c.halved = 0;
     if (c.state != 0) return;
     if (c.b > 2 && ratio_halves(T, c.set, c.u, c.b)) {
@@ -389,22 +470,55 @@ __global__ void k_big_decide(TreeDev T, BigCell *big, int nb)
     }
 }
 
-// Clear the histogram of every cell whose b was just halved.
-__global__ void __launch_bounds__(256) k_big_zero(const BigCell *big, int nb, int *hist, int total)
+__global__ void k_big_decide(TreeDev T, LevelBufs L)
 {
+    if (T.ctr->abort) return;
+    const int nb = T.ctr->nbig;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x)
+        decide_cell(T, L.big[i]);
+}
+
+
+// Clear the histogram of every cell whose b was just halved.
+__global__ void __launch_bounds__(256) k_big_zero(const Counters *ctr, LevelBufs L)
+{
+    if (ctr->abort) return;
+    const int nb = ctr->nbig;
+    const int total = ctr->hist_total;
+    const BigCell *big = L.big;
+    int *hist = L.hist;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         const BigCell &c = big[find_cell_by_hist(big, nb, e)];
         if (c.halved) hist[e] = 0;
     }
 }
 
+// One thread, after a ratio pass: another pass iff some cell halved b.
+__global__ void k_ratio_end(Counters *ctr, cudaGraphConditionalHandle h, int graph)
+{
+    ctr->ratio_it += 1;
+    ctr->ratio_total += 1;
+    const int go = ctr->again && !ctr->abort && ctr->ratio_it < 16;
+    ctr->again = 0;
+    ctr->ratio_go = go;
+    if (graph) cudaGraphSetConditional(h, go);
+}
+
 // After acceptance, one thread per cell: no-progress guard, walk
 // parameters, sub-cell widths, slot placement.
-__global__ void k_big_finish(TreeDev T, BigCell *big, int nb, int slot_level_base)
+__device__ void finish_cell(const TreeDev &T, BigCell &c, int slot_level_base);
+
+__global__ void k_big_finish(TreeDev T, LevelBufs L)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
-    BigCell &c = big[i];
+    if (T.ctr->abort) return;
+    const int nb = T.ctr->nbig;
+    const int base = T.ctr->slot_base;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x)
+        finish_cell(T, L.big[i], base);
+}
+
+__device__ void finish_cell(const TreeDev &T, BigCell &c, int slot_level_base)
+{
     const int b = c.b;
     const NodeGeom g = T.geom[c.node];
     for (int l = 0; l < 3; l++) c.w[l] = cell_width(g.lo[l], g.hi[l], b);
@@ -440,11 +554,18 @@ __global__ void k_big_finish(TreeDev T, BigCell *big, int nb, int slot_level_bas
 
 // Emit the sub-cells of every accepted big cell: slots, child nodes, queues,
 // leaf work units; cursor[e] = first tree position of sub-cell e.
-__global__ void __launch_bounds__(256) k_big_emit(TreeDev T, const BigCell *big, int nb,
-                                                  const int *hist, const int *hoff, int *cursor,
-                                                  int dst_buf, int *next_big, SmallItem *small)
+__global__ void __launch_bounds__(256) k_big_emit(TreeDev T, LevelBufs L)
 {
-    const int total = T.ctr->hist_total;
+    Counters *ctr = T.ctr;
+    if (ctr->abort) return;
+    const int nb = ctr->nbig;
+    const int total = ctr->hist_total;
+    const int dst_buf = ctr->level & 1;
+    const BigCell *big = L.big;
+    const int *hist = L.hist, *hoff = L.hoff;
+    int *cursor = L.cursor;
+    int *next_big = L.ids[(ctr->level + 1) & 1];
+    SmallItem *small = L.small;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         int ci = find_cell_by_hist(big, nb, e);
         const BigCell c = big[ci];
@@ -475,7 +596,13 @@ __global__ void __launch_bounds__(256) k_big_emit(TreeDev T, const BigCell *big,
                 cg.set = c.set;
                 T.geom[child] = cg;
                 if (cnt > kSmallCap) {
-                    next_big[atomicAdd(&T.ctr->nbig_next, 1)] = child;
+                    const int k = atomicAdd(&T.ctr->nbig_next, 1);
+                    if (k < L.cap_big) {
+                        next_big[k] = child;
+                    } else {
+                        atomicOr(&T.ctr->status, kStCapBig);
+                        T.ctr->abort = 1;
+                    }
                 } else {
                     int k = atomicAdd(&T.ctr->nsmall, 1);
                     if (k < T.cap_small) small[k] = SmallItem{child, dst_buf};
@@ -496,10 +623,17 @@ __global__ void __launch_bounds__(256) k_big_emit(TreeDev T, const BigCell *big,
 // Move every particle of an accepted big cell to its sub-cell.  Leaf
 // sub-cells are final: they go straight to tree order; others to the
 // working buffer `dst` for the next level / the warp builder.
-__global__ void __launch_bounds__(256) k_big_scatter(TreeDev T, const BigCell *big, int nb, Src src,
-                                                     int *cursor, float4 *dst_pos, float *dst_h)
+__global__ void __launch_bounds__(256) k_big_scatter(TreeDev T, LevelBufs L)
 {
-    const int total = T.ctr->chunk_total;
+    const Counters *ctr = T.ctr;
+    if (ctr->abort) return;
+    const int nb = ctr->nbig;
+    const int total = ctr->chunk_total;
+    const BigCell *big = L.big;
+    const Src src = level_src(L, ctr->level);
+    int *cursor = L.cursor;
+    float4 *dst_pos = L.wpos[ctr->level & 1];
+    float *dst_h = L.wh[ctr->level & 1];
     for (int chunk = blockIdx.x; chunk < total; chunk += gridDim.x) {
         int ci = find_cell_by_chunk(big, nb, chunk);
         BigCell c = big[ci];
@@ -536,24 +670,34 @@ __global__ void __launch_bounds__(256) k_big_scatter(TreeDev T, const BigCell *b
 // Exclusive scan of int32 counts (sums fit in int32).
 constexpr int kScanTile = 4096;
 
-__global__ void __launch_bounds__(256) k_scan_tiles(const int *in, int n, int *tile_sum)
+// The scans below run over the level histogram: n = hist_total (nothing
+// when the build was aborted).
+__device__ __forceinline__ int scan_n(const Counters *ctr) { return ctr->abort ? 0 : ctr->hist_total; }
+
+__global__ void __launch_bounds__(256) k_scan_tiles(const Counters *ctr, const int *in, int *tile_sum)
 {
-    int t0 = blockIdx.x * kScanTile;
-    int s = 0;
-    for (int i = t0 + threadIdx.x; i < min(t0 + kScanTile, n); i += blockDim.x) s += in[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(~0u, s, o);
+    const int n = scan_n(ctr);
+    const int ntiles = (n + kScanTile - 1) / kScanTile;
     __shared__ int ws[8];
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int t = 0;
-        for (int k = 0; k < 8; k++) t += ws[k];
-        tile_sum[blockIdx.x] = t;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int t0 = tile * kScanTile;
+        int s = 0;
+        for (int i = t0 + threadIdx.x; i < min(t0 + kScanTile, n); i += blockDim.x) s += in[i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(~0u, s, o);
+        if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int k = 0; k < 8; k++) t += ws[k];
+            tile_sum[tile] = t;
+        }
+        __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(1024) k_scan_tile_sums(int *tile_sum, int ntiles)
+__global__ void __launch_bounds__(1024) k_scan_tile_sums(const Counters *ctr, int *tile_sum)
 {
+    const int ntiles = (scan_n(ctr) + kScanTile - 1) / kScanTile;
     __shared__ int sh[1024];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
@@ -576,11 +720,21 @@ __global__ void __launch_bounds__(1024) k_scan_tile_sums(int *tile_sum, int ntil
     }
 }
 
-__global__ void __launch_bounds__(256) k_scan_apply(const int *in, int n, const int *tile_off, int *out)
+__device__ void scan_apply_tile(const int *in, int n, int tile, const int *tile_off, int *out);
+
+__global__ void __launch_bounds__(256) k_scan_apply(const Counters *ctr, const int *in,
+                                                    const int *tile_off, int *out)
 {
-    // 256 threads x 16 items
+    const int n = scan_n(ctr);
+    const int ntiles = (n + kScanTile - 1) / kScanTile;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) scan_apply_tile(in, n, tile, tile_off, out);
+}
+
+// 256 threads x 16 items of one tile.
+__device__ void scan_apply_tile(const int *in, int n, int tile, const int *tile_off, int *out)
+{
     __shared__ int ws[8];
-    int t0 = blockIdx.x * kScanTile;
+    int t0 = tile * kScanTile;
     int v[16];
     int s = 0;
     for (int k = 0; k < 16; k++) {
@@ -598,12 +752,13 @@ __global__ void __launch_bounds__(256) k_scan_apply(const int *in, int n, const 
     __syncthreads();
     int woff = 0;
     for (int k = 0; k < wid; k++) woff += ws[k];
-    int run = tile_off[blockIdx.x] + woff + incl - s;
+    int run = tile_off[tile] + woff + incl - s;
     for (int k = 0; k < 16; k++) {
         int i = t0 + threadIdx.x * 16 + k;
         if (i < n) out[i] = run;
         run += v[k];
     }
+    __syncthreads();  // ws is reused by the block's next tile
 }
 
 // ------------------------------------------------------------------ warp builder
@@ -638,9 +793,10 @@ __device__ __forceinline__ int warp_sum(int v)
 
 // One warp builds the whole sub-tree of one cell of <= kSmallCap particles.
 __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const SmallItem *items,
-                                                            int nitems, Src src0, Src src1,
-                                                            Src srcin)
+                                                            Src src0, Src src1, Src srcin)
 {
+    if (T.ctr->abort) return;
+    const int nitems = min(T.ctr->nsmall, T.cap_small);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmallSmem &S = reinterpret_cast<SmallSmem *>(smem_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
@@ -913,93 +1069,81 @@ void launch_bbox(const TreeDev &T, const float *x, const float *y, const float *
                                                              T.set_bbox, T.ctr);
 }
 
-void launch_root_sets(const TreeDev &T, int *big_ids, SmallItem *small, cudaStream_t st)
+void launch_roots(const TreeDev &T, const LevelBufs &L, int sms, cudaStream_t st)
 {
     note_launch();
-    k_root_sets<<<grid_for(T.nsets, 128, 1 << 16), 128, 0, st>>>(T, big_ids, small);
+    k_root_sets<<<grid_for(T.nsets, 128, 1 << 16), 128, 0, st>>>(T, L);
+    note_launch();
+    k_copy_leaf_roots<<<grid_for(T.n, 256, sms * 8), 256, 0, st>>>(T, L.in.x, L.in.y, L.in.z, L.in.h);
 }
 
-void launch_copy_leaf_roots(const TreeDev &T, const float *x, const float *y, const float *z,
-                            const float *h, int sms, cudaStream_t st)
+void launch_level_go(Counters *ctr, int advance, cudaGraphConditionalHandle h, int graph, cudaStream_t st)
 {
     note_launch();
-    k_copy_leaf_roots<<<grid_for(T.n, 256, sms * 8), 256, 0, st>>>(T, x, y, z, h);
+    k_level_go<<<1, 1, 0, st>>>(ctr, advance, h, graph);
 }
 
-void launch_big_setup(const TreeDev &T, BigCell *big, const int *ids, int nb, cudaStream_t st)
+void launch_level_start(const TreeDev &T, const LevelBufs &L, const LevelHints &H, int sms,
+                        cudaGraphConditionalHandle hratio, int graph, cudaStream_t st)
 {
     note_launch();
-    k_big_setup<<<grid_for(nb, 256, 1 << 20), 256, 0, st>>>(T, big, ids, nb);
+    k_level_begin<<<1, 1, 0, st>>>(T.ctr);
     note_launch();
-    k_big_scan<<<1, 1024, 0, st>>>(big, nb, T.ctr);
+    k_big_setup<<<grid_for(H.nbig, 256, sms * 4), 256, 0, st>>>(T, L);
+    note_launch();
+    k_big_scan<<<1, 1024, 0, st>>>(T, L, hratio, graph);
 }
 
-void launch_big_hist(const TreeDev &T, const BigCell *big, int nb, int chunks, Src src, int *hist,
-                     int sms, cudaStream_t st)
+void launch_level_zero(const TreeDev &T, const LevelBufs &L, const LevelHints &H, int sms, cudaStream_t st)
 {
     note_launch();
-    k_big_hist<<<grid_for(chunks, 1, sms * 8), 256, 0, st>>>(T, big, nb, src, hist);
+    k_zero_hist<<<grid_for(H.hist, 256 * 4, sms * 8), 256, 0, st>>>(T.ctr, L.hist);
 }
 
-void launch_big_ratio(const TreeDev &T, BigCell *big, int nb, const int *hist, int hist_total, int sms,
-                      cudaStream_t st)
+void launch_ratio_pass(const TreeDev &T, const LevelBufs &L, const LevelHints &H, int sms,
+                       cudaGraphConditionalHandle hratio, int graph, cudaStream_t st)
 {
     note_launch();
-    k_big_count<<<grid_for(hist_total, 256, sms * 8), 256, 0, st>>>(T, big, nb, hist, hist_total);
+    k_big_hist<<<grid_for(H.chunks, 1, sms * 8), 256, 0, st>>>(T, L);
     note_launch();
-    k_big_decide<<<grid_for(nb, 128, 1 << 20), 128, 0, st>>>(T, big, nb);
+    k_big_count<<<grid_for(H.hist, 256, sms * 8), 256, 0, st>>>(T, L);
+    note_launch();
+    k_big_decide<<<grid_for(H.nbig, 128, sms * 4), 128, 0, st>>>(T, L);
+    note_launch();
+    k_big_zero<<<grid_for(H.hist, 256, sms * 8), 256, 0, st>>>(T.ctr, L);
+    note_launch();
+    k_ratio_end<<<1, 1, 0, st>>>(T.ctr, hratio, graph);
 }
 
-void launch_big_zero(const BigCell *big, int nb, int *hist, int hist_total, int sms, cudaStream_t st)
+void launch_level_finish(const TreeDev &T, const LevelBufs &L, const LevelHints &H, int sms,
+                         cudaGraphConditionalHandle hlevel, int graph, cudaStream_t st)
 {
+    const int tiles = (int)((H.hist + kScanTile - 1) / kScanTile);
     note_launch();
-    k_big_zero<<<grid_for(hist_total, 256, sms * 8), 256, 0, st>>>(big, nb, hist, hist_total);
+    k_big_finish<<<grid_for(H.nbig, 128, sms * 4), 128, 0, st>>>(T, L);
+    note_launch();
+    k_scan_tiles<<<grid_for(tiles, 1, sms * 8), 256, 0, st>>>(T.ctr, L.hist, L.tiles);
+    note_launch();
+    k_scan_tile_sums<<<1, 1024, 0, st>>>(T.ctr, L.tiles);
+    note_launch();
+    k_scan_apply<<<grid_for(tiles, 1, sms * 8), 256, 0, st>>>(T.ctr, L.hist, L.tiles, L.hoff);
+    note_launch();
+    k_big_emit<<<grid_for(H.hist, 256, sms * 16), 256, 0, st>>>(T, L);
+    note_launch();
+    k_big_scatter<<<grid_for(H.chunks, 1, sms * 8), 256, 0, st>>>(T, L);
+    launch_level_go(T.ctr, 1, hlevel, graph, st);
 }
 
-void launch_big_finish(const TreeDev &T, BigCell *big, int nb, int slot_level_base, cudaStream_t st)
-{
-    note_launch();
-    k_big_finish<<<grid_for(nb, 128, 1 << 20), 128, 0, st>>>(T, big, nb, slot_level_base);
-}
+int scan_tile_count(long long n) { return (int)((n + kScanTile - 1) / kScanTile) + 1; }
 
-void launch_scan(const int *in, int n, int *tile_buf, int *out, cudaStream_t st)
+void launch_small(const TreeDev &T, const LevelBufs &L, long long nitems_hint, int sms, cudaStream_t st)
 {
-    int ntiles = (n + kScanTile - 1) / kScanTile;
-    if (ntiles < 1) ntiles = 1;
+    if (nitems_hint <= 0) return;
+    const Src s0{nullptr, nullptr, nullptr, nullptr, L.wpos[0], L.wh[0]};
+    const Src s1{nullptr, nullptr, nullptr, nullptr, L.wpos[1], L.wh[1]};
+    int blocks = grid_for(nitems_hint, kSmallWarps, sms * 4);
     note_launch();
-    k_scan_tiles<<<ntiles, 256, 0, st>>>(in, n, tile_buf);
-    note_launch();
-    k_scan_tile_sums<<<1, 1024, 0, st>>>(tile_buf, ntiles);
-    note_launch();
-    k_scan_apply<<<ntiles, 256, 0, st>>>(in, n, tile_buf, out);
-}
-
-int scan_tile_count(int n) { return (n + kScanTile - 1) / kScanTile + 1; }
-
-void launch_big_emit(const TreeDev &T, const BigCell *big, int nb, int hist_total, const int *hist,
-                     const int *hoff, int *cursor, int dst_buf, int *next_big, SmallItem *small,
-                     int sms, cudaStream_t st)
-{
-    note_launch();
-    k_big_emit<<<grid_for(hist_total, 256, sms * 16), 256, 0, st>>>(T, big, nb, hist, hoff, cursor,
-                                                                     dst_buf, next_big, small);
-}
-
-void launch_big_scatter(const TreeDev &T, const BigCell *big, int nb, int chunks, Src src,
-                        int *cursor, float4 *dst_pos, float *dst_h, int sms, cudaStream_t st)
-{
-    note_launch();
-    k_big_scatter<<<grid_for(chunks, 1, sms * 8), 256, 0, st>>>(T, big, nb, src, cursor, dst_pos,
-                                                                dst_h);
-}
-
-void launch_small(const TreeDev &T, const SmallItem *items, int nitems, Src src0, Src src1,
-                  Src srcin, int sms, cudaStream_t st)
-{
-    if (nitems <= 0) return;
-    int blocks = grid_for(nitems, kSmallWarps, sms * 4);
-    note_launch();
-    k_small<<<blocks, 32 * kSmallWarps, small_smem_bytes(), st>>>(T, items, nitems, src0, src1, srcin);
+    k_small<<<blocks, 32 * kSmallWarps, small_smem_bytes(), st>>>(T, L.small, s0, s1, L.in);
 }
 
 cudaError_t build_init_attributes()
@@ -1008,24 +1152,17 @@ cudaError_t build_init_attributes()
                                 (int)small_smem_bytes());
 }
 
-__global__ void k_init_counters(Counters *ctr)
+__global__ void k_init_counters(Counters *ctr, int nroots)
 {
     Counters c = {};
+    c.nnodes = nroots;  // nodes 0 .. nroots-1 are the set roots
     *ctr = c;
 }
 
-__global__ void k_set_int(int *p, int v) { *p = v; }
-
-void launch_init_counters(Counters *ctr, cudaStream_t st)
+void launch_init_counters(Counters *ctr, int nroots, cudaStream_t st)
 {
     note_launch();
-    k_init_counters<<<1, 1, 0, st>>>(ctr);
-}
-
-void launch_set_int(int *p, int v, cudaStream_t st)
-{
-    note_launch();
-    k_set_int<<<1, 1, 0, st>>>(p, v);
+    k_init_counters<<<1, 1, 0, st>>>(ctr, nroots);
 }
 
 }  // namespace bt

@@ -595,10 +595,13 @@ __global__ void __launch_bounds__(kFindThreads, 4) k_find(FindArgs A)
     FindSmem &S = *reinterpret_cast<FindSmem *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const TreeDev &T = A.T;
-    const int nchunks = (A.ngroups + kFindChunk - 1) / kFindChunk;
+    // ngroups < 0: read the count the build left on the device (graph form)
+    const int ngroups = A.ngroups >= 0 ? A.ngroups
+                                       : (T.ctr->abort ? 0 : min(T.ctr->ngroups, T.cap_groups));
+    const int nchunks = (ngroups + kFindChunk - 1) / kFindChunk;
 
     for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
-        const int g1 = min(chunk * kFindChunk + kFindChunk, A.ngroups);
+        const int g1 = min(chunk * kFindChunk + kFindChunk, ngroups);
         for (int g = chunk * kFindChunk; g < g1; g++) {
             __syncthreads();
             if (DENS)
@@ -753,13 +756,24 @@ __global__ void k_mass_to_tree(const float4 *__restrict__ spos, const float *__r
 
 size_t find_smem_bytes() { return sizeof(FindSmem); }
 
+static int g_find_per_sm[2] = {1, 1};  // resident blocks per SM of k_find<false>, k_find<true>
+
 cudaError_t find_init_attributes()
 {
     cudaError_t e = cudaFuncSetAttribute(k_find<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(FindSmem));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_find<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(FindSmem));
+    e = cudaFuncSetAttribute(k_find<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(FindSmem));
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_find_per_sm[0], k_find<false>, kFindThreads,
+                                                      sizeof(FindSmem));
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_find_per_sm[1], k_find<true>, kFindThreads,
+                                                      sizeof(FindSmem));
+    for (int k = 0; k < 2; k++)
+        if (g_find_per_sm[k] < 1) g_find_per_sm[k] = 1;
+    return e;
 }
 
 cudaError_t launch_find(const TreeDev &T, int ngroups, int ngmax, int32_t *nbrs, int32_t *counts,
@@ -772,23 +786,22 @@ cudaError_t launch_find(const TreeDev &T, int ngroups, int ngmax, int32_t *nbrs,
     A.counts = counts;
     A.smass = smass;
     A.rho = rho;
-    A.ngroups = ngroups;
-    if (ngroups <= 0) return cudaSuccess;
-    int per_sm = 0;
+    A.ngroups = ngroups;  // < 0: the count is read on the device
+    if (ngroups == 0) return cudaSuccess;
     const bool dens = rho != nullptr;
     if (dens) {
         int nb = (T.n + 255) / 256;
         if (nb > sms * 8) nb = sms * 8;
+        if (nb < 1) nb = 1;
         note_launch();
         k_mass_to_tree<<<nb, 256, 0, st>>>(T.spos, m, smass, T.n);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_find<true>, kFindThreads, sizeof(FindSmem));
-    } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_find<false>, kFindThreads, sizeof(FindSmem));
     }
-    if (per_sm < 1) per_sm = 1;
-    long long nchunks = (ngroups + kFindChunk - 1) / kFindChunk;
+    const int per_sm = g_find_per_sm[dens ? 1 : 0];
     long long blocks = (long long)sms * per_sm;
-    if (blocks > nchunks) blocks = nchunks;
+    if (ngroups > 0) {
+        const long long nchunks = (ngroups + kFindChunk - 1) / kFindChunk;
+        if (blocks > nchunks) blocks = nchunks;
+    }
     note_launch();
     if (dens)
         k_find<true><<<(int)blocks, kFindThreads, sizeof(FindSmem), st>>>(A);

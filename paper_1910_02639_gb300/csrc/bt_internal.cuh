@@ -234,15 +234,25 @@ struct Counters {
     int find_next;     // dynamic work counter of the find kernels
     int hist_total;    // sum of b0^3 over this level's big cells
     int chunk_total;   // blocks of kBigChunk particles over this level's big cells
-    int pad[2];
+    int level;         // big-cell level being built (0 = the set roots)
+    int nbig;          // big cells of this level
+    int slot_base;     // first sub-cell of this level's big cells
+    int ratio_it;      // ratio-test passes of this level
+    int ratio_total;   // ratio-test passes over all levels
+    int ratio_go;      // another ratio pass follows
+    int level_go;      // another level follows
+    int abort;         // capacity or input problem: the remaining kernels do nothing
+    long long hist_need;  // histogram entries a level asked for (on abort)
 };
 
 // Per big cell of the current level.
 struct BigCell {
     int node;
     int b0, b;
-    int hist_base;     // offset into the level histogram
-    int chunk_base;    // first kBigChunk block of this cell
+    int hist_n;        // b0^3 (histogram entries reserved)
+    int chunk_n;       // kBigChunk blocks of the cell
+    int hist_base;     // offset into the level histogram (prefix of hist_n)
+    int chunk_base;    // first kBigChunk block of this cell (prefix of chunk_n)
     int state;         // 0 pending, 1 accepted, 2 stays a leaf
     int slot0;
     int u;             // sub-cells with n_j <= alpha s (current b)
@@ -344,5 +354,27 @@ struct Src {
         return pos[p];
     }
 };
+
+// Buffers of the level-synchronous build of big cells.  Level L reads the
+// particles from the input (L = 0) or working buffer (L-1)&1 and writes
+// working buffer L&1; its big cells are ids[L&1], the next level's ids[(L+1)&1].
+struct LevelBufs {
+    Src in;
+    float4 *wpos[2];
+    float *wh[2];
+    int *ids[2];
+    BigCell *big;
+    int *hist, *hoff, *cursor, *tiles;
+    SmallItem *small;
+    long long cap_hist;
+    int cap_big, cap_tiles;
+};
+
+__device__ __forceinline__ Src level_src(const LevelBufs &L, int level)
+{
+    if (level == 0) return L.in;
+    const int k = (level - 1) & 1;
+    return Src{nullptr, nullptr, nullptr, nullptr, L.wpos[k], L.wh[k]};
+}
 
 }  // namespace bt

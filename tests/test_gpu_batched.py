@@ -207,3 +207,97 @@ def test_autotuner_table_and_params(bt):
     _, _, got = run_batched(bt, sets, params)
     for i in range(len(sets)):
         _assert_same(got[i], ref[i], "set %d tuned" % i)
+
+
+# ------------------------------------------------------------------ graph form
+def run_graph(bt, sets, params=None, ngmax=NGMAX, tree=None, density=True, bufs=None):
+    import torch
+    dev = torch.device("cuda:0")
+    off, *arrs = _concat(sets)
+    n = int(off[-1])
+    if bufs is None:
+        x, y, z, h, m = (torch.from_numpy(a).to(dev) for a in arrs)
+        nb = torch.full((max(n, 1) * ngmax,), -1, dtype=torch.int32, device=dev)
+        cnt = torch.full((max(n, 1),), -7, dtype=torch.int32, device=dev)
+        rho = torch.empty(max(n, 1), dtype=torch.float32, device=dev)
+    else:
+        x, y, z, h, m, nb, cnt, rho = bufs
+        for d, a in zip((x, y, z, h, m), arrs):
+            d.copy_(torch.from_numpy(a))
+        nb.fill_(-1)
+    tree = bt.btree_build_find_batched(x, y, z, h, off, ngmax, nb, cnt,
+                                       m=m if density else None, rho=rho if density else None,
+                                       params=params, tree=tree)
+    torch.cuda.synchronize()
+    nbh = nb.view(-1, ngmax)[:n].cpu().numpy()
+    cnth, rhoh = cnt[:n].cpu().numpy(), rho[:n].cpu().numpy()
+    out = [dict(nb=nbh[off[i]:off[i + 1]], cnt=cnth[off[i]:off[i + 1]],
+                rho=rhoh[off[i]:off[i + 1]]) for i in range(len(sets))]
+    return tree, off, out, (x, y, z, h, m, nb, cnt, rho)
+
+
+def test_graph_form_equals_separate_calls(bt):
+    sets = _mixed_sets()
+    t0, _, ref = run_batched(bt, sets)
+    t0.free()
+    t1, _, got, _ = run_graph(bt, sets)
+    info = bt.btree_get_info(t1)
+    assert info["num_groups"] > 0 and info["max_depth"] >= 2
+    t1.free()
+    for i in range(len(sets)):
+        _assert_same(got[i], ref[i], "set %d graph" % i)
+
+
+def test_graph_relaunch_with_new_parameters_and_new_inputs(bt):
+    sets = wl.batched_sets(9, seed=519, nmin=300, nmax=40_000)
+    _, _, ref = run_batched(bt, sets)
+    tree, off, got, bufs = run_graph(bt, sets)
+    for i in range(len(sets)):
+        _assert_same(got[i], ref[i], "first launch, set %d" % i)
+    # same buffers and sizes: the captured graph is relaunched; per-set
+    # parameters are read on the device at each launch
+    for params in (dict(bucket_size=8, beta=0.25), dict(bucket_size=64, group_size=16), None):
+        tree, _, got, bufs = run_graph(bt, sets, params=params, tree=tree, bufs=bufs)
+        for i in range(len(sets)):
+            _assert_same(got[i], ref[i], "relaunch %s, set %d" % (params, i))
+    # other inputs of another size through the same handle: a new capture
+    sets2 = wl.batched_sets(5, seed=520, nmin=1000, nmax=80_000)
+    _, _, ref2 = run_batched(bt, sets2)
+    tree, _, got2, _ = run_graph(bt, sets2, tree=tree)
+    for i in range(len(sets2)):
+        _assert_same(got2[i], ref2[i], "recapture, set %d" % i)
+    tree.free()
+
+
+def test_graph_form_without_density_and_plummer_tails(bt, oracle):
+    sets = [wl.plummer(3000, seed=521, target=120), wl.plummer(20_000, seed=522, target=90),
+            wl.uniform_cube(5000, seed=523, target=70)]
+    tree, _, got, _ = run_graph(bt, sets, density=False, ngmax=512)
+    tree.free()
+    for i, s in enumerate(sets):
+        ref_nb, ref_cnt = oracle.OracleTree(s.x, s.y, s.z, bucket_size=16).find(s.h, 512)
+        assert np.array_equal(got[i]["cnt"], ref_cnt), "set %d counts" % i
+        used = np.arange(512)[None, :] < np.minimum(ref_cnt, 512)[:, None]
+        assert np.array_equal(np.where(used, ref_nb, -1), got[i]["nb"]), "set %d lists" % i
+
+
+def test_graph_form_rejects_nonfinite_and_recovers(bt):
+    bad = wl.uniform_cube(3000, seed=524, target=50)
+    bad.x[17] = np.nan
+    good = wl.uniform_cube(3000, seed=525, target=50)
+    with pytest.raises(bt.BtreeError) as ei:
+        run_graph(bt, [good, bad])
+    assert ei.value.status == bt.BT_ERR_NONFINITE
+    _, _, ref = run_batched(bt, [good])
+    tree, _, got, _ = run_graph(bt, [good])
+    _assert_same(got[0], ref[0], "after a rejected input")
+    tree.free()
+
+
+def test_graph_form_counts_its_kernels(bt):
+    sets = wl.batched_sets(6, seed=526, nmin=2000, nmax=60_000)
+    l0 = bt.btree_kernel_launches()
+    tree, _, _, _ = run_graph(bt, sets)
+    l1 = bt.btree_kernel_launches()
+    tree.free()
+    assert 20 <= l1 - l0 <= 400
