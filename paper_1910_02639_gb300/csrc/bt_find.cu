@@ -360,6 +360,52 @@ __device__ __forceinline__ void sort_keys(uint32_t *buf)
     block_sort<kSortThreads, E>(buf);
 }
 
+// Packed pairs of FP32 lanes (sm_100+ f32x2 arithmetic, round-to-nearest per
+// element, the same results as the scalar operations).
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Stage A for two candidates per lane (one from each of two chunks): the
+// squared FP32 distances to query P, two at a time.  Same arithmetic as
+// test_chunk: d2 = fma(dz, dz, fma(dy, dy, dx * dx)).
+__device__ __forceinline__ void dist2_pair(const float4 &P, unsigned long long qx,
+                                           unsigned long long qy, unsigned long long qz, float &d1,
+                                           float &d2)
+{
+    const unsigned long long dx = f2_sub(qx, f2_pack(P.x, P.x));
+    const unsigned long long dy = f2_sub(qy, f2_pack(P.y, P.y));
+    const unsigned long long dz = f2_sub(qz, f2_pack(P.z, P.z));
+    const unsigned long long r = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+    f2_unpack(r, d1, d2);
+}
+
 // One FP32 filter step of stage A: the ballot of hits of query P over this
 // lane's candidate Q, and whether the pair lies in the uncertain band.
 __device__ __forceinline__ unsigned test_chunk(const float4 &P, float rhi, const float4 &Q,
@@ -437,11 +483,18 @@ __device__ void group_window(const FindArgs &A, FindSmem &S, bool presorted)
         if (v1) Q1 = S.cand[S.key[k1] & (kCap - 1)];
         if (v2) Q2 = S.cand[S.key[k2] & (kCap - 1)];
         bool amb1 = false, amb2 = false;
+        const unsigned long long qx = f2_pack(Q1.x, Q2.x), qy = f2_pack(Q1.y, Q2.y),
+                                 qz = f2_pack(Q1.z, Q2.z);
         for (int p = 0; p < gcount; p++) {
             const float4 P = S.q[p];
             const float rhi = S.qrhi[p];
-            const unsigned b1 = test_chunk(P, rhi, Q1, v1, amb1);
-            const unsigned b2 = test_chunk(P, rhi, Q2, v2, amb2);
+            float d1, d2;
+            dist2_pair(P, qx, qy, qz, d1, d2);
+            const bool h1 = v1 && d1 < P.w, h2 = v2 && d2 < P.w;
+            amb1 |= v1 && !h1 && d1 <= rhi;
+            amb2 |= v2 && !h2 && d2 <= rhi;
+            const unsigned b1 = __ballot_sync(~0u, h1);
+            const unsigned b2 = __ballot_sync(~0u, h2);
             if (lane == 0) {
                 S.mask[p * kChunks + c] = b1;
                 if (has2) S.mask[p * kChunks + c2] = b2;
@@ -502,17 +555,31 @@ __device__ void group_window(const FindArgs &A, FindSmem &S, bool presorted)
             }
             __syncwarp();
             const int nb = min(kHitBatch, total - b0);
-            for (int i = i0; i < nb; i += 32) {
-                const uint32_t key = S.key[hl[i]];
+            // two list positions per step (i, i + 32) so that their
+            // shared-memory loads overlap; the density terms are still
+            // added in position order
+            for (int i = i0; i < nb; i += 64) {
+                const bool two = i + 32 < nb;
+                const uint32_t key1 = S.key[hl[i]];
+                const uint32_t key2 = two ? S.key[hl[i + 32]] : 0u;
                 const int pos = base + b0 + i;
-                if (pos < A.ngmax) row[pos] = kmin - S.set_lo + (int)(key >> kSlotBits);
+                const int vbase = kmin - S.set_lo;
+                if (pos < A.ngmax) row[pos] = vbase + (int)(key1 >> kSlotBits);
+                if (two && pos + 32 < A.ngmax) row[pos + 32] = vbase + (int)(key2 >> kSlotBits);
                 if (DENS) {
-                    const int slot = key & (kCap - 1);
-                    const float4 Q = S.cand[slot];
-                    const float dx = Q.x - P.x, dy = Q.y - P.y, dz = Q.z - P.z;
-                    const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    const float q = d2 > 0.0f ? d2 * rsqrtf(d2) * inv_h : 0.0f;
-                    acc = fmaf(S.cmass[slot], m4_shape(q), acc);
+                    const int s1 = key1 & (kCap - 1), s2 = key2 & (kCap - 1);
+                    const float4 Q1 = S.cand[s1];
+                    const float4 Q2 = S.cand[s2];
+                    const float m1 = S.cmass[s1], m2 = S.cmass[s2];
+                    const float dx1 = Q1.x - P.x, dy1 = Q1.y - P.y, dz1 = Q1.z - P.z;
+                    const float dx2 = Q2.x - P.x, dy2 = Q2.y - P.y, dz2 = Q2.z - P.z;
+                    const float e1 = fmaf(dz1, dz1, fmaf(dy1, dy1, dx1 * dx1));
+                    const float e2 = fmaf(dz2, dz2, fmaf(dy2, dy2, dx2 * dx2));
+                    const float q1 = e1 > 0.0f ? e1 * rsqrtf(e1) * inv_h : 0.0f;
+                    const float q2 = e2 > 0.0f ? e2 * rsqrtf(e2) * inv_h : 0.0f;
+                    const float w1 = m4_shape(q1), w2 = m4_shape(q2);
+                    acc = fmaf(m1, w1, acc);
+                    if (two) acc = fmaf(m2, w2, acc);
                 }
             }
             __syncwarp();
