@@ -6,7 +6,9 @@ per-level sub-cell histograms / ratio test / scan / scatter, warp-level
 sub-trees) + FindNeighbors fused with the M4 density (walk, gather, sort,
 test, ordered capped rows).  Default workload: the jittered lattice slab of
 1e7 particles (400 x 250 x 100, spacing 1, jitter +-0.1, h = 1.5, masses 1/N),
-bucket size 16, ngmax 256.
+ngmax 256.  Before timing, the autotuner picks this set's bucket size, beta,
+work-unit size and find block shape (none changes a result; `config` names
+the choice, `default_params` times the untuned s = 16 default beside it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -201,10 +203,31 @@ def run_gpu(args):
     rho = torch.empty(n, dtype=torch.float32, device=dev)
     tree = None
 
+    # ---- parameters: the autotuner's choice for this set (bucket size, beta,
+    # work-unit size, find block shape); none of them changes a result
+    params = dict(bucket_size=sb, alpha=cfg["alpha"], beta=cfg["beta"])
+    tune_s = 0.0
+    if args.params:
+        params.update(json.loads(args.params))
+    elif not args.no_tune:
+        from paper_1910_02639_gb300.autotune import Tuner
+        t_tune = time.time()
+        tuner = Tuner(dev, ngmax, stream=stream)
+        tuner.tune([s])
+        params = tuner.params_for([s])[0]
+        tune_s = time.time() - t_tune
+        del tuner
+        torch.cuda.empty_cache()
+    cfg.update(bucket_size=params["bucket_size"], beta=params["beta"],
+               work_unit=params.get("group_size") or 32,
+               find_shape="4 warps, 512-candidate window" if params.get("find_compact")
+               else "8 warps, 1024-candidate window",
+               tuned=not args.no_tune and not args.params)
+    offs = [0, n]
+
     def step():
         nonlocal tree
-        tree = bt.btree_build(x, y, z, h, bucket_size=sb, alpha=cfg["alpha"], beta=cfg["beta"],
-                              stream=stream, tree=tree)
+        tree = bt.btree_build_batched(x, y, z, h, offs, params, stream=stream, tree=tree)
         bt.btree_find_neighbors_density(tree, m, ngmax, nb, cnt, rho, stream=stream)
 
     for _ in range(args.warmup):
@@ -227,8 +250,7 @@ def run_gpu(args):
     e0.record(stream)
     build_ms = []
     for k in range(K):
-        tree = bt.btree_build(x, y, z, h, bucket_size=sb, alpha=cfg["alpha"], beta=cfg["beta"],
-                              stream=stream, tree=tree)
+        tree = bt.btree_build_batched(x, y, z, h, offs, params, stream=stream, tree=tree)
         build_ms.append(bt.btree_get_info(tree)["build_ms"])
         f0[k].record(stream)
         bt.btree_find_neighbors_density(tree, m, ngmax, nb, cnt, rho, stream=stream)
@@ -239,26 +261,40 @@ def run_gpu(args):
     launches = bt.btree_kernel_launches() - l0
     step_ms = e0.elapsed_time(e1) / K
 
+    # ---- the untuned default: btree_build (s = 16, alpha = beta = 0.5) + find
+    dtree = None
+    for _ in range(3):
+        dtree = bt.btree_build(x, y, z, h, bucket_size=sb, alpha=cfg["alpha"], beta=cfg["beta"],
+                               stream=stream, tree=dtree)
+        bt.btree_find_neighbors_density(dtree, m, ngmax, nb, cnt, rho, stream=stream)
+    barrier(dist, dev)
+    e0.record(stream)
+    for k in range(K):
+        dtree = bt.btree_build(x, y, z, h, bucket_size=sb, alpha=cfg["alpha"], beta=cfg["beta"],
+                               stream=stream, tree=dtree)
+        bt.btree_find_neighbors_density(dtree, m, ngmax, nb, cnt, rho, stream=stream)
+    e1.record(stream)
+    barrier(dist, dev)
+    default_ms = e0.elapsed_time(e1) / K
+    dtree.free()
+
     # ---- the same step as one CUDA graph (btree_build_find_batched, one set)
     gtree = None
     off = [0, n]
     t_cap = time.perf_counter()
     gtree = bt.btree_build_find_batched(x, y, z, h, off, ngmax, nb, cnt, m=m, rho=rho,
-                                        params=dict(bucket_size=sb, alpha=cfg["alpha"], beta=cfg["beta"]),
-                                        stream=stream, tree=gtree)
+                                        params=params, stream=stream, tree=gtree)
     capture_ms = (time.perf_counter() - t_cap) * 1e3
     for _ in range(2):
         gtree = bt.btree_build_find_batched(x, y, z, h, off, ngmax, nb, cnt, m=m, rho=rho,
-                                            params=dict(bucket_size=sb, alpha=cfg["alpha"],
-                                                        beta=cfg["beta"]), stream=stream, tree=gtree)
+                                            params=params, stream=stream, tree=gtree)
     g0 = bt.btree_kernel_launches()
     barrier(dist, dev)
     t0g = time.time()
     e0.record(stream)
     for k in range(K):
         gtree = bt.btree_build_find_batched(x, y, z, h, off, ngmax, nb, cnt, m=m, rho=rho,
-                                            params=dict(bucket_size=sb, alpha=cfg["alpha"],
-                                                        beta=cfg["beta"]), stream=stream, tree=gtree)
+                                            params=params, stream=stream, tree=gtree)
     e1.record(stream)
     barrier(dist, dev)
     t1g = time.time()
@@ -292,6 +328,11 @@ def run_gpu(args):
            "build_ms": round(statistics.mean(build_ms), 4), "find_ms": round(find_ms, 4),
            "roofline": roofline, "step_roofline": step_roofline,
            "gpu_launches": int(launches),
+           "tuning_s": round(tune_s, 2),
+           "default_params": {"ms_per_step": reduce_max(dist, default_ms, dev),
+                              "value": pairs * ws / (reduce_max(dist, default_ms, dev) * 1e-3),
+                              "form": "btree_build (s=16, alpha=beta=0.5, 8-warp find) + "
+                                      "btree_find_neighbors_density, untuned"},
            "graph_form": {"ms_per_step": reduce_max(dist, graph_ms, dev),
                           "value": graph_pairs * ws / (reduce_max(dist, graph_ms, dev) * 1e-3),
                           "gpu_launches": int(graph_launches), "first_call_ms": round(capture_ms, 3),
@@ -310,7 +351,7 @@ def run_gpu(args):
 
     # ---- end to end through the public API, host buffers
     if not args.no_e2e:
-        out["e2e"] = run_e2e(args, bt, s, cfg, dev, stream, dist, ws, pairs)
+        out["e2e"] = run_e2e(args, bt, s, cfg, dev, stream, dist, ws, pairs, params)
 
     # ---- CPU oracle on the host cores (rank 0, N = 1)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -322,7 +363,7 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, bt, s, cfg, dev, stream, dist, ws, pairs):
+def run_e2e(args, bt, s, cfg, dev, stream, dist, ws, pairs, params):
     import torch
     n, ngmax = s.n, cfg["ngmax"]
     hx = [torch.from_numpy(a).pin_memory() for a in (s.x, s.y, s.z, s.h, s.m)]
@@ -339,8 +380,8 @@ def run_e2e(args, bt, s, cfg, dev, stream, dist, ws, pairs):
         nonlocal tree
         for d, hsrc in zip(dx, hx):
             d.copy_(hsrc, non_blocking=True)
-        tree = bt.btree_build(dx[0], dx[1], dx[2], dx[3], bucket_size=cfg["bucket_size"],
-                              alpha=cfg["alpha"], beta=cfg["beta"], stream=stream, tree=tree)
+        tree = bt.btree_build_batched(dx[0], dx[1], dx[2], dx[3], [0, n], params, stream=stream,
+                                      tree=tree)
         bt.btree_find_neighbors_density(tree, dx[4], ngmax, nb, cnt, rho, stream=stream)
         h_nb.copy_(nb, non_blocking=True)
         h_cnt.copy_(cnt, non_blocking=True)
@@ -426,7 +467,7 @@ def run_batched_section(args, bt, dev, stream, dist, rank, ws):
                                                 for v in (plain_ms, batched_ms, tuned_ms, graph_ms))
     ds.free()
     rate = lambda ms: all_pairs / (ms * 1e-3)
-    table = {str(k): {kk: v[kk] for kk in ("bucket_size", "beta", "group_size")}
+    table = {str(k): {kk: v[kk] for kk in ("bucket_size", "beta", "group_size", "find_compact")}
              for k, v in tuner.table.items()}
     return {"workload": f"batched_{args.batched_sets}_sets", "n": int(sum(sp[1] for sp in specs)),
             "nsets": len(specs), "ngmax": ngmax, "scaling": "strong", "sets_per_rank": len(mine),
@@ -589,6 +630,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--params", default="",
+                    help='fixed set parameters as JSON (no tuning), e.g. {"find_compact": true}')
     ap.add_argument("--batched-sets", type=int, default=256)
     ap.add_argument("--batched-steps", type=int, default=5)
     ap.add_argument("--no-serving", action="store_true")

@@ -1,16 +1,21 @@
 """Autotuner for the batched b-tree: per size class of particle set, the
-bucket size s, the empty-cell limit beta (Eq. 4) and the find work-unit size
-(queries searched together) that minimise build + find + density time.
+bucket size s, the empty-cell limit beta (Eq. 4), the find work-unit size
+(queries searched together) and the find block shape (8 warps and a
+1024-candidate window, or 4 warps and 512) that minimise build + find +
+density time.
 
-None of the three changes a result: the neighbour lists are defined without
+None of the knobs changes a result: the neighbour lists are defined without
 reference to the tree, and the density of a particle is summed in the order
 of its sorted list.  So the tuner only times.
 
-Search: coordinate descent from (s = 16, beta = 0.5, 32 queries) -- s first,
-then beta, then the work-unit size -- on a sample of the sets of each size
+Search: coordinate descent from (wide shape, s = 16, beta = 0.5, 32 queries)
+-- the block shape first, then s, beta and the work-unit size -- on a sample
+of the sets of each size
 class (half-decades of n), each candidate timed with CUDA events after a
-warm-up run.  The table maps a size class to its parameters and can be saved
-and loaded as JSON.
+warm-up run; a change is kept only if it is more than `margin` (3 %) faster
+than the best so far, so that timing noise does not move the choice.  The
+table maps a size class to its parameters and can be saved and loaded as
+JSON.
 """
 from __future__ import annotations
 
@@ -23,8 +28,9 @@ SPACE = {
     "bucket_size": (8, 16, 32, 64),
     "beta": (0.25, 0.5, 0.75),
     "group_size": (16, 32),
+    "find_compact": (False, True),
 }
-START = {"bucket_size": 16, "beta": 0.5, "group_size": 32}
+START = {"bucket_size": 16, "beta": 0.5, "group_size": 32, "find_compact": False}
 
 
 def size_class(n: int) -> int:
@@ -33,14 +39,15 @@ def size_class(n: int) -> int:
 
 
 class Tuner:
-    def __init__(self, device, ngmax: int, stream=None, reps: int = 2,
-                 sample_particles: int = 2_000_000, space=None):
+    def __init__(self, device, ngmax: int, stream=None, reps: int = 3,
+                 sample_particles: int = 2_000_000, space=None, margin: float = 0.03):
         self.device = device
         self.ngmax = ngmax
         self.stream = stream
         self.reps = reps
         self.sample_particles = sample_particles
         self.space = dict(space or SPACE)
+        self.margin = margin
         self.table: dict[int, dict] = {}
         self.trials = 0
 
@@ -74,13 +81,13 @@ class Tuner:
         try:
             cur = dict(START)
             best = self._time(ds, dict(DEFAULT_PARAMS, **cur))
-            for key in ("bucket_size", "beta", "group_size"):
+            for key in ("find_compact", "bucket_size", "beta", "group_size"):
                 for v in self.space[key]:
                     if v == cur[key]:
                         continue
                     cand = dict(cur, **{key: v})
                     t = self._time(ds, dict(DEFAULT_PARAMS, **cand))
-                    if t < best:
+                    if t < best * (1.0 - self.margin):  # a change must beat timing noise
                         best, cur = t, cand
             return dict(cur, ms=best)
         finally:
@@ -101,7 +108,8 @@ class Tuner:
             p = dict(DEFAULT_PARAMS)
             e = self.table.get(size_class(s.n))
             if e:
-                p.update(bucket_size=e["bucket_size"], beta=e["beta"], group_size=e["group_size"])
+                p.update(bucket_size=e["bucket_size"], beta=e["beta"], group_size=e["group_size"],
+                         find_compact=e["find_compact"])
             out.append(p)
         return out
 

@@ -72,7 +72,7 @@ struct btree {
     SetRec *set_rec = nullptr;  // device copy of the staged records
     SetRec *h_rec = nullptr;    // [cap_sets] pinned staging
 
-    int ngroups = 0;
+    int ngroups = 0, ngroups_c = 0;  // work units of the wide / compact lists
     bt_info info{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int64_t hist_need_seen = 0;  // largest level histogram asked for so far
@@ -324,11 +324,12 @@ int finish_build(btree *t, cudaStream_t st)
 {
     const Counters &c = *t->hctr;
     if (c.status & kStNonfinite) return BT_ERR_NONFINITE;
-    if (c.abort || (c.status & kCapBits)) {
+    if (c.abort || (c.status & kCapBits) || (int64_t)c.ngroups + c.ngroups_c > t->cap_groups) {
         t->hist_need_seen = std::max<int64_t>(t->hist_need_seen, c.hist_need);
         return kRetry;
     }
     t->ngroups = c.ngroups;
+    t->ngroups_c = c.ngroups_c;
     NodeWalk w0;
     w0.b = 0;
     if (t->nsets > 0) cudaMemcpyAsync(&w0, t->walk, sizeof(NodeWalk), cudaMemcpyDeviceToHost, st);
@@ -344,7 +345,7 @@ int finish_build(btree *t, cudaStream_t st)
     I.max_depth = c.max_depth;
     I.num_nodes = c.nnodes;
     I.num_slots = c.nslots;
-    I.num_groups = c.ngroups;
+    I.num_groups = c.ngroups + c.ngroups_c;
     I.root_b = w0.b;
     I.num_oversized = c.noversized;
     I.build_ms = ms;
@@ -456,7 +457,7 @@ cudaError_t capture_step(btree *t, const GraphKey &K, cudaGraph_t *out)
     }
     launch_small(T, L, t->cap_small, t->sms, s0);
     record_event(t->ev1, s0, true);
-    if (K.nbrs) chk(launch_find(T, -1, K.ngmax, K.nbrs, K.counts, K.m, K.smass, K.rho, t->sms, s0));
+    if (K.nbrs) chk(launch_find(T, -1, -1, K.ngmax, K.nbrs, K.counts, K.m, K.smass, K.rho, t->sms, s0));
     cudaGraph_t g = nullptr;
     chk(cudaStreamEndCapture(s0, &g));
     if (err != cudaSuccess) {
@@ -668,7 +669,7 @@ static int stage_batched(const float *x, const float *y, const float *z, const f
         const int s = params ? params[i].bucket_size : 16;
         const double a = params ? params[i].alpha : 0.5, b = params ? params[i].beta : 0.5;
         if (s < 1 || s > (1 << 20) || !is_finite_d(a) || !is_finite_d(b)) return BT_ERR_ARG;
-        if (params && (params[i].flags & ~BT_SET_OCTREE)) return BT_ERR_ARG;
+        if (params && (params[i].flags & ~(BT_SET_OCTREE | BT_SET_FIND_COMPACT))) return BT_ERR_ARG;
         if (params && (params[i].group_size < 0 || params[i].group_size > kGroupMax)) return BT_ERR_ARG;
         smin = std::min(smin, s);
     }
@@ -684,7 +685,8 @@ static int stage_batched(const float *x, const float *y, const float *z, const f
     for (int i = 0; i < nsets; i++) {
         const int s = params ? params[i].bucket_size : 16;
         const double a = params ? params[i].alpha : 0.5, b = params ? params[i].beta : 0.5;
-        const int f = params && (params[i].flags & BT_SET_OCTREE) ? kSetOctree : 0;
+        const int f = (params && (params[i].flags & BT_SET_OCTREE) ? kSetOctree : 0) |
+                      (params && (params[i].flags & BT_SET_FIND_COMPACT) ? kSetFindCompact : 0);
         const int g = params && params[i].group_size > 0 ? params[i].group_size : kGroupMax;
         stage_set(t, i, offsets[i], offsets[i + 1], s, a, b, f, g);
     }
@@ -728,7 +730,7 @@ int btree_find_neighbors(const btree_t *t, int ngmax, int32_t *neighbors, int32_
     if (!t || ngmax < 1 || (t->n > 0 && (!neighbors || !counts))) return BT_ERR_ARG;
     if (t->n == 0) return BT_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    return to_status(launch_find(view(t), t->ngroups, ngmax, neighbors, counts, nullptr, nullptr,
+    return to_status(launch_find(view(t), t->ngroups, t->ngroups_c, ngmax, neighbors, counts, nullptr, nullptr,
                                  nullptr, t->sms, st));
 }
 
@@ -747,7 +749,7 @@ int btree_find_neighbors_density(const btree_t *tc, const float *m, int ngmax, i
         if (!ok) return BT_ERR_OOM;
         t->cap_smass = t->n;
     }
-    return to_status(launch_find(view(t), t->ngroups, ngmax, neighbors, counts, m, t->smass, rho,
+    return to_status(launch_find(view(t), t->ngroups, t->ngroups_c, ngmax, neighbors, counts, m, t->smass, rho,
                                  t->sms, st));
 }
 
@@ -758,7 +760,7 @@ int btree_find_neighbors_density_noalloc(const btree_t *t, const float *m, int n
     if (!t || ngmax < 1 || (t->n > 0 && (!neighbors || !counts || !m || !rho))) return BT_ERR_ARG;
     if (t->n > noalloc_max_particles()) return BT_ERR_CAPACITY;
     if (t->n == 0) return BT_OK;
-    return to_status(launch_find_density_noalloc(view(t), t->ngroups, ngmax, neighbors, counts, m,
+    return to_status(launch_find_density_noalloc(view(t), t->ngroups, t->ngroups_c, ngmax, neighbors, counts, m,
                                                  rho, t->sms, static_cast<cudaStream_t>(stream)));
 }
 

@@ -22,15 +22,19 @@
 namespace bt {
 
 // Work units of at most the set's gmax particles over tree positions
-// [start, start + cnt).
+// [start, start + cnt).  Sets searched by the compact block shape fill the
+// groups array from its end, the others from its start.
 __device__ __forceinline__ void emit_groups(const TreeDev &T, int set, int start, int cnt)
 {
     const int gm = T.set_gmax[set];
     const int ng = (cnt + gm - 1) / gm;
-    const int g0 = atomicAdd(&T.ctr->ngroups, ng);
-    for (int q = 0; q < ng; q++)
-        if (g0 + q < T.cap_groups)
-            T.groups[g0 + q] = make_int2(start + q * gm, group_pack(set, min(gm, cnt - q * gm)));
+    const bool compact = (T.set_flags[set] & kSetFindCompact) != 0;
+    const int g0 = atomicAdd(compact ? &T.ctr->ngroups_c : &T.ctr->ngroups, ng);
+    for (int q = 0; q < ng; q++) {
+        if (g0 + q >= T.cap_groups) break;
+        const int idx = compact ? T.cap_groups - 1 - (g0 + q) : g0 + q;
+        T.groups[idx] = make_int2(start + q * gm, group_pack(set, min(gm, cnt - q * gm)));
+    }
     if (g0 + ng > T.cap_groups) atomicOr(&T.ctr->status, kStCapGroups);
 }
 

@@ -33,13 +33,21 @@
 
 namespace bt {
 
-constexpr int kFindThreads = 256;
-constexpr int kFindWarps = kFindThreads / 32;
-constexpr int kCap = 1024;                 // candidates per window
-constexpr int kSlotBits = 10;              // log2(kCap)
+// Two block shapes, chosen per particle set (BT_SET_FIND_COMPACT): 8 warps
+// per work unit with a 1024-candidate window, or 4 warps with a 512-candidate
+// window (more work units resident per SM).  Same results.
+template <int NT_, int CAP_, int SLOT_BITS_>
+struct FindCfg {
+    static constexpr int NT = NT_;              // threads per work unit
+    static constexpr int WARPS = NT_ / 32;
+    static constexpr int CAP = CAP_;            // candidates per window
+    static constexpr int SLOT_BITS = SLOT_BITS_;  // log2(CAP)
+    static constexpr int CHUNKS = CAP_ / 32;
+    static constexpr int JOB_MAX = CAP_ / 2;    // 32-particle jobs per group walk
+};
+using CfgWide = FindCfg<256, 1024, 10>;
+using CfgCompact = FindCfg<128, 512, 9>;
 constexpr int kSpanMax = (1 << 22) - 1;    // original-index span of one window
-constexpr int kChunks = kCap / 32;
-constexpr int kJobMax = 512;               // 32-particle jobs per group walk
 constexpr int kFrontMax = 64;              // tree nodes per walk frontier
 constexpr int kDescendMin = 32;            // smaller internal sub-cells are scanned whole
 constexpr int kFindChunk = 4;              // consecutive groups per block step
@@ -48,17 +56,18 @@ constexpr int kUnroll = 4;                 // gather jobs in flight per warp
 constexpr int kSortThreads = 128;          // warps 0-3 sort; the others wait
 constexpr float kPiF = 3.14159265358979f;
 
+template <class C>
 struct FindSmem {
-    float4 cand[kCap];        // x, y, z, original index (bits)
-    float cmass[kCap];
-    uint32_t key[kCap];       // (orig - kmin) << kSlotBits | slot, sorted
-    uint32_t mask[kGroupMax * kChunks];
+    float4 cand[C::CAP];        // x, y, z, original index (bits)
+    float cmass[C::CAP];
+    uint32_t key[C::CAP];       // (orig - kmin) << C::SLOT_BITS | slot, sorted
+    uint32_t mask[kGroupMax * C::CHUNKS];
     // density partial sums: slot k of query p holds the terms whose position
     // in p's ascending neighbour list is k mod 32, so the summation order
     // depends on the list alone (not on windows or work-unit composition)
     float qacc[kGroupMax][32];
-    unsigned short hits[kFindWarps][kHitBatch];
-    int2 jobs[kJobMax];       // (first tree position, length <= 32)
+    unsigned short hits[C::WARPS][kHitBatch];
+    int2 jobs[C::JOB_MAX];       // (first tree position, length <= 32)
     float4 q[kGroupMax];      // x, y, z, R_lo
     float qrhi[kGroupMax];
     float qh[kGroupMax];
@@ -72,7 +81,7 @@ struct FindSmem {
     float box[13];            // PL[3] PH[3] QL[3] QH[3] T
     int njobs, nfront, nnext, ncand, kmin, kmax, range_ovf, ovf_lo, ovf_hi;
     int jfail, cover, gstart, gcount, whi, ctot;
-    int wcnt[2][kFindWarps];  // per-warp kept counts (scan mode), double-buffered
+    int wcnt[2][C::WARPS];  // per-warp kept counts (scan mode), double-buffered
     int gset, set_lo, set_hi;  // the group's particle set and its index range
 };
 
@@ -83,7 +92,8 @@ struct FindArgs {
     int32_t *counts;
     const float *smass;  // masses in tree order (density only)
     float *rho;
-    int ngroups;
+    int ngroups;  // >= 0: work units of this list; < 0: read on the device
+    int list;     // 0: the wide-shape list (front of T.groups); 1: the compact list (back)
 };
 
 __device__ __forceinline__ float warp_min(float v)
@@ -110,13 +120,14 @@ __device__ __forceinline__ bool exact_neighbor(float4 p, float hp, float4 qd)
 }
 
 // Append a contiguous particle range as 32-particle jobs.
-__device__ __forceinline__ void add_range(FindSmem &S, int s, int len)
+template <class C>
+__device__ __forceinline__ void add_range(FindSmem<C> &S, int s, int len)
 {
     if (len <= 0) return;
     const int nj = (len + 31) >> 5;
     atomicAdd(&S.ctot, len);
     const int j0 = atomicAdd(&S.njobs, nj);
-    if (j0 + nj <= kJobMax) {
+    if (j0 + nj <= C::JOB_MAX) {
         for (int k = 0; k < nj; k++) S.jobs[j0 + k] = make_int2(s + 32 * k, min(32, len - 32 * k));
     } else {
         // jobs [0, jfail) were all written; everything else is covered by
@@ -130,7 +141,8 @@ __device__ __forceinline__ void add_range(FindSmem &S, int s, int len)
 
 // All threads: the tree walk for the group's query box, one frontier of
 // nodes at a time; the rows of all frontier nodes are spread over the block.
-__device__ void group_walk(const TreeDev &T, FindSmem &S)
+template <class C>
+__device__ void group_walk(const TreeDev &T, FindSmem<C> &S)
 {
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -138,7 +150,7 @@ __device__ void group_walk(const TreeDev &T, FindSmem &S)
         S.ctot = 0;
         S.cover = 0;
         S.range_ovf = 0;
-        S.jfail = kJobMax;
+        S.jfail = C::JOB_MAX;
         S.ovf_lo = INT_MAX;
         S.ovf_hi = INT_MIN;
         S.front[0][0] = S.gset;  // root of the group's set
@@ -194,7 +206,7 @@ __device__ void group_walk(const TreeDev &T, FindSmem &S)
         }
         __syncthreads();
         const int total = S.fr_off[nf];
-        for (int r = tid; r < total; r += kFindThreads) {
+        for (int r = tid; r < total; r += C::NT) {
             int lo = 0, hi = nf - 1;  // frontier node owning row r
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
@@ -242,7 +254,7 @@ __device__ void group_walk(const TreeDev &T, FindSmem &S)
         // (a superset, and no particle appears twice).
         if (tid < 32) {
             int lo = S.ovf_lo, hi = S.ovf_hi;
-            const int nj = min(S.jfail, kJobMax);
+            const int nj = min(S.jfail, C::JOB_MAX);
             for (int r = tid; r < nj; r += 32) {
                 const int2 jb = S.jobs[r];
                 lo = min(lo, jb.x);
@@ -267,8 +279,8 @@ __device__ void group_walk(const TreeDev &T, FindSmem &S)
 // Stream the candidates of the collected jobs.  mode 0: collect those with
 // original index in [wlo, whi) into the buffer; mode 1: histogram them into
 // 256 bins of width W starting at wlo.
-template <bool DENS>
-__device__ void group_gather(const FindArgs &A, FindSmem &S, int mode, int wlo, int whi, int W)
+template <bool DENS, class C>
+__device__ void group_gather(const FindArgs &A, FindSmem<C> &S, int mode, int wlo, int whi, int W)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float PL0 = S.box[0], PL1 = S.box[1], PL2 = S.box[2];
@@ -279,7 +291,7 @@ __device__ void group_gather(const FindArgs &A, FindSmem &S, int mode, int wlo, 
     const int2 cv = S.jobs[0];
     const unsigned lt = (1u << lane) - 1;
     int kmin = INT_MAX, kmax = INT_MIN;
-    for (int j0 = warp * kUnroll; j0 < njobs; j0 += kFindWarps * kUnroll) {
+    for (int j0 = warp * kUnroll; j0 < njobs; j0 += C::WARPS * kUnroll) {
         float4 c[kUnroll];
         float mm[kUnroll];
         bool keep[kUnroll];
@@ -322,7 +334,7 @@ __device__ void group_gather(const FindArgs &A, FindSmem &S, int mode, int wlo, 
             for (int u = 0; u < kUnroll; u++) {
                 if (keep[u]) {
                     const int slot = base + __popc(bal[u] & lt);
-                    if (slot < kCap) {
+                    if (slot < C::CAP) {
                         S.cand[slot] = c[u];
                         if (DENS) S.cmass[slot] = mm[u];
                     }
@@ -418,34 +430,35 @@ __device__ __forceinline__ unsigned test_chunk(const float4 &P, float rhi, const
     return __ballot_sync(~0u, hit);
 }
 
-__device__ __forceinline__ void fix_band(FindSmem &S, int c, int gcount, const float4 &Q, int lane)
+template <class C>
+__device__ __forceinline__ void fix_band(FindSmem<C> &S, int c, int gcount, const float4 &Q, int lane)
 {
     for (int p = 0; p < gcount; p++) {
         const float4 P = S.q[p];
         const float dx = Q.x - P.x, dy = Q.y - P.y, dz = Q.z - P.z;
         const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         if (!(d2 < P.w) && d2 <= S.qrhi[p] && exact_neighbor(P, S.qh[p], Q))
-            atomicOr(&S.mask[p * kChunks + c], 1u << lane);
+            atomicOr(&S.mask[p * C::CHUNKS + c], 1u << lane);
     }
 }
 
 // Sort, test and emit the candidates of the current window.
 // `presorted`: the candidates were collected in ascending original index
 // and their keys are already in S.key (scan mode).
-template <bool DENS>
-__device__ void group_window(const FindArgs &A, FindSmem &S, bool presorted)
+template <bool DENS, class C>
+__device__ void group_window(const FindArgs &A, FindSmem<C> &S, bool presorted)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m = S.ncand;  // <= kCap here
+    const int m = S.ncand;  // <= C::CAP here
     const int gcount = S.gcount;
     if (m == 0) return;
     const int kmin = S.kmin;
     if (!presorted) {
         int npad = kSortThreads;
         while (npad < m) npad <<= 1;
-        for (int s = tid; s < npad; s += kFindThreads) {
+        for (int s = tid; s < npad; s += C::NT) {
             uint32_t k = 0xffffffffu;
-            if (s < m) k = ((uint32_t)(__float_as_int(S.cand[s].w) - kmin) << kSlotBits) | (uint32_t)s;
+            if (s < m) k = ((uint32_t)(__float_as_int(S.cand[s].w) - kmin) << C::SLOT_BITS) | (uint32_t)s;
             S.key[s] = k;
         }
         __syncthreads();
@@ -454,7 +467,9 @@ __device__ void group_window(const FindArgs &A, FindSmem &S, bool presorted)
             case kSortThreads: sort_keys<1>(S.key); break;
             case 2 * kSortThreads: sort_keys<2>(S.key); break;
             case 4 * kSortThreads: sort_keys<4>(S.key); break;
-            default: sort_keys<8>(S.key); break;
+            default:
+                if constexpr (C::CAP > 4 * kSortThreads) sort_keys<8>(S.key);
+                break;
             }
         }
         __syncthreads();
@@ -467,21 +482,21 @@ __device__ void group_window(const FindArgs &A, FindSmem &S, bool presorted)
         int lo = 0, hi = m;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if ((S.key[mid] >> kSlotBits) < want) lo = mid + 1; else hi = mid;
+            if ((S.key[mid] >> C::SLOT_BITS) < want) lo = mid + 1; else hi = mid;
         }
-        S.qself[tid] = (o >= kmin && lo < m && (S.key[lo] >> kSlotBits) == want) ? lo : -1;
+        S.qself[tid] = (o >= kmin && lo < m && (S.key[lo] >> C::SLOT_BITS) == want) ? lo : -1;
     }
 
     // ---- stage A: one ballot per (query, chunk); two chunks per pass
     const int nch = (m + 31) >> 5;
-    for (int c = warp; c < nch; c += 2 * kFindWarps) {
-        const int c2 = c + kFindWarps;
+    for (int c = warp; c < nch; c += 2 * C::WARPS) {
+        const int c2 = c + C::WARPS;
         const bool has2 = c2 < nch;
         const int k1 = c * 32 + lane, k2 = c2 * 32 + lane;
         const bool v1 = k1 < m, v2 = k2 < m;
         float4 Q1 = make_float4(0.f, 0.f, 0.f, 0.f), Q2 = Q1;
-        if (v1) Q1 = S.cand[S.key[k1] & (kCap - 1)];
-        if (v2) Q2 = S.cand[S.key[k2] & (kCap - 1)];
+        if (v1) Q1 = S.cand[S.key[k1] & (C::CAP - 1)];
+        if (v2) Q2 = S.cand[S.key[k2] & (C::CAP - 1)];
         bool amb1 = false, amb2 = false;
         const unsigned long long qx = f2_pack(Q1.x, Q2.x), qy = f2_pack(Q1.y, Q2.y),
                                  qz = f2_pack(Q1.z, Q2.z);
@@ -496,8 +511,8 @@ __device__ void group_window(const FindArgs &A, FindSmem &S, bool presorted)
             const unsigned b1 = __ballot_sync(~0u, h1);
             const unsigned b2 = __ballot_sync(~0u, h2);
             if (lane == 0) {
-                S.mask[p * kChunks + c] = b1;
-                if (has2) S.mask[p * kChunks + c2] = b2;
+                S.mask[p * C::CHUNKS + c] = b1;
+                if (has2) S.mask[p * C::CHUNKS + c2] = b2;
             }
         }
         __syncwarp();
@@ -515,8 +530,8 @@ __device__ void group_window(const FindArgs &A, FindSmem &S, bool presorted)
     // ---- stage B: per query, compact the ballots into hit positions, then
     // write the row (and the density terms) lane-parallel in ascending order.
     unsigned short *hl = S.hits[warp];
-    for (int p = warp; p < gcount; p += kFindWarps) {
-        uint32_t mk = lane < nch ? S.mask[p * kChunks + lane] : 0u;
+    for (int p = warp; p < gcount; p += C::WARPS) {
+        uint32_t mk = lane < nch ? S.mask[p * C::CHUNKS + lane] : 0u;
         const int sr = S.qself[p];
         if (sr >= 0 && lane == (sr >> 5)) mk &= ~(1u << (sr & 31));
         const int cnt = __popc(mk);
@@ -564,10 +579,10 @@ __device__ void group_window(const FindArgs &A, FindSmem &S, bool presorted)
                 const uint32_t key2 = two ? S.key[hl[i + 32]] : 0u;
                 const int pos = base + b0 + i;
                 const int vbase = kmin - S.set_lo;
-                if (pos < A.ngmax) row[pos] = vbase + (int)(key1 >> kSlotBits);
-                if (two && pos + 32 < A.ngmax) row[pos + 32] = vbase + (int)(key2 >> kSlotBits);
+                if (pos < A.ngmax) row[pos] = vbase + (int)(key1 >> C::SLOT_BITS);
+                if (two && pos + 32 < A.ngmax) row[pos + 32] = vbase + (int)(key2 >> C::SLOT_BITS);
                 if (DENS) {
-                    const int s1 = key1 & (kCap - 1), s2 = key2 & (kCap - 1);
+                    const int s1 = key1 & (C::CAP - 1), s2 = key2 & (C::CAP - 1);
                     const float4 Q1 = S.cand[s1];
                     const float4 Q2 = S.cand[s2];
                     const float m1 = S.cmass[s1], m2 = S.cmass[s2];
@@ -593,10 +608,10 @@ __device__ void group_window(const FindArgs &A, FindSmem &S, bool presorted)
 // Scan mode, for a group whose query box holds a large part of its set (very
 // large h): instead of re-streaming the candidates once per window, walk the
 // set in ascending original index through the inverse permutation, keep the
-// particles inside the box, and cut windows of at most kCap candidates that
-// arrive already sorted.  Block-wide: one round = kFindThreads indices.
-template <bool DENS>
-__device__ void group_scan(const FindArgs &A, FindSmem &S)
+// particles inside the box, and cut windows of at most C::CAP candidates that
+// arrive already sorted.  Block-wide: one round = C::NT indices.
+template <bool DENS, class C>
+__device__ void group_scan(const FindArgs &A, FindSmem<C> &S)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float PL0 = S.box[0], PL1 = S.box[1], PL2 = S.box[2];
@@ -610,8 +625,8 @@ __device__ void group_scan(const FindArgs &A, FindSmem &S)
         const int kmin = j0;
         int base = 0;  // candidates kept so far in this window (same in all threads)
         int j = j0;
-        for (; j < jend; j += kFindThreads) {
-            if (j - kmin > kSpanMax - kFindThreads) break;  // keys must fit their bits
+        for (; j < jend; j += C::NT) {
+            if (j - kmin > kSpanMax - C::NT) break;  // keys must fit their bits
             const int idx = j + tid;
             bool keep = false;
             float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -630,18 +645,18 @@ __device__ void group_scan(const FindArgs &A, FindSmem &S)
             __syncthreads();
             int before = 0, tot = 0;
 #pragma unroll
-            for (int w = 0; w < kFindWarps; w++) {
+            for (int w = 0; w < C::WARPS; w++) {
                 const int v = S.wcnt[buf][w];
                 before += w < warp ? v : 0;
                 tot += v;
             }
             buf ^= 1;
-            if (base + tot > kCap) break;  // uniform: this round opens the next window
+            if (base + tot > C::CAP) break;  // uniform: this round opens the next window
             if (keep) {
                 const int slot = base + before + __popc(bal & lt);
                 S.cand[slot] = c;
                 if (DENS) S.cmass[slot] = mm;
-                S.key[slot] = ((uint32_t)(idx - kmin) << kSlotBits) | (uint32_t)slot;
+                S.key[slot] = ((uint32_t)(idx - kmin) << C::SLOT_BITS) | (uint32_t)slot;
             }
             base += tot;
         }
@@ -655,16 +670,22 @@ __device__ void group_scan(const FindArgs &A, FindSmem &S)
     }
 }
 
-template <bool DENS>
-__global__ void __launch_bounds__(kFindThreads, 4) k_find(FindArgs A)
+template <class C, bool DENS>
+__global__ void __launch_bounds__(C::NT, 1024 / C::NT) k_find(FindArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    FindSmem &S = *reinterpret_cast<FindSmem *>(smem_raw);
+    FindSmem<C> &S = *reinterpret_cast<FindSmem<C> *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const TreeDev &T = A.T;
-    // ngroups < 0: read the count the build left on the device (graph form)
-    const int ngroups = A.ngroups >= 0 ? A.ngroups
-                                       : (T.ctr->abort ? 0 : min(T.ctr->ngroups, T.cap_groups));
+    // ngroups < 0: read the count the build left on the device (graph form).
+    // The wide-shape list runs forward from the start of T.groups, the
+    // compact one backward from its end (clamped so that both stay inside).
+    int ngroups = A.ngroups;
+    if (ngroups < 0) {
+        const int nf = T.ctr->abort ? 0 : min(T.ctr->ngroups, T.cap_groups);
+        ngroups = A.list == 0 ? nf : (T.ctr->abort ? 0 : min(T.ctr->ngroups_c, T.cap_groups - nf));
+    }
+    const int2 *G = A.list == 0 ? T.groups : T.groups + (T.cap_groups - ngroups);
     const int nchunks = (ngroups + kFindChunk - 1) / kFindChunk;
 
     for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
@@ -672,11 +693,11 @@ __global__ void __launch_bounds__(kFindThreads, 4) k_find(FindArgs A)
         for (int g = chunk * kFindChunk; g < g1; g++) {
             __syncthreads();
             if (DENS)
-                for (int i = tid; i < kGroupMax * 32; i += kFindThreads) (&S.qacc[0][0])[i] = 0.0f;
+                for (int i = tid; i < kGroupMax * 32; i += C::NT) (&S.qacc[0][0])[i] = 0.0f;
             // ---- queries (warp 0), FP32 only: RN(2h * 2h) is the float
             // rounding of the exact binary64 (2h)^2.
             if (tid < 32) {
-                const int2 grp0 = T.groups[g];
+                const int2 grp0 = G[g];
                 const int2 grp = make_int2(grp0.x, group_count(grp0.y));
                 const bool v = lane < grp.y;
                 float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -731,10 +752,10 @@ __global__ void __launch_bounds__(kFindThreads, 4) k_find(FindArgs A)
             group_walk(T, S);
 
             // ---- scan mode when re-streaming the candidates per window would
-            // cost more than one pass over the whole set (C^2 / kCap > 3/4 n)
+            // cost more than one pass over the whole set (C^2 / C::CAP > 3/4 n)
             const long long ctot = S.ctot;
             const long long nset = S.set_hi - S.set_lo;
-            const bool scan = ctot > 2 * kCap && 3 * nset * kCap < 4 * ctot * ctot;
+            const bool scan = ctot > 2 * C::CAP && 3 * nset * C::CAP < 4 * ctot * ctot;
             if (scan && tid == 0) atomicOr(&T.ctr->status, kStWalk);
             if (scan) group_scan<DENS>(A, S);
 
@@ -751,21 +772,21 @@ __global__ void __launch_bounds__(kFindThreads, 4) k_find(FindArgs A)
                 __syncthreads();
                 group_gather<DENS>(A, S, 0, wlo, whi, 1);
                 __syncthreads();
-                const bool fits = S.ncand <= kCap && (S.ncand == 0 || S.kmax - S.kmin < kSpanMax);
+                const bool fits = S.ncand <= C::CAP && (S.ncand == 0 || S.kmax - S.kmin < kSpanMax);
                 if (!fits) {
                     // choose the largest window [wlo, whi) that fits, by histograms
                     long long span = (long long)wend - wlo;
                     if (tid == 0) atomicOr(&T.ctr->status, kStWalk);
                     for (;;) {
                         const int Wd = (int)((span + 255) / 256);
-                        for (int i = tid; i < 256; i += kFindThreads) S.hist[i] = 0;
+                        for (int i = tid; i < 256; i += C::NT) S.hist[i] = 0;
                         __syncthreads();
                         group_gather<DENS>(A, S, 1, wlo, (int)min((long long)INT_MAX, wlo + span), Wd);
                         __syncthreads();
                         if (tid == 0) {
                             long long cum = 0;
                             int k = 0;
-                            while (k < 256 && (long long)k * Wd < span && cum + S.hist[k] <= kCap &&
+                            while (k < 256 && (long long)k * Wd < span && cum + S.hist[k] <= C::CAP &&
                                    (long long)(k + 1) * Wd <= kSpanMax) {
                                 cum += S.hist[k];
                                 k++;
@@ -800,7 +821,7 @@ __global__ void __launch_bounds__(kFindThreads, 4) k_find(FindArgs A)
                 if (c > A.ngmax) atomicOr(&T.ctr->status, kStNgmax);
             }
             if (DENS) {
-                for (int p = warp; p < S.gcount; p += kFindWarps) {
+                for (int p = warp; p < S.gcount; p += C::WARPS) {
                     float a = S.qacc[p][lane];
                     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(~0u, a, o);
                     if (lane == 0) {
@@ -821,30 +842,56 @@ __global__ void k_mass_to_tree(const float4 *__restrict__ spos, const float *__r
         smass[t] = m[__float_as_int(spos[t].w)];
 }
 
-size_t find_smem_bytes() { return sizeof(FindSmem); }
+size_t find_smem_bytes() { return sizeof(FindSmem<CfgWide>); }
 
-static int g_find_per_sm[2] = {1, 1};  // resident blocks per SM of k_find<false>, k_find<true>
+// resident blocks per SM of k_find<CfgWide/CfgCompact, false/true>
+static int g_find_per_sm[2][2] = {{1, 1}, {1, 1}};
 
-cudaError_t find_init_attributes()
+template <class C, bool DENS>
+static cudaError_t find_attr(int *per_sm)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_find<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(FindSmem));
+    cudaError_t e = cudaFuncSetAttribute(k_find<C, DENS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(FindSmem<C>));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_find<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(FindSmem));
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_find_per_sm[0], k_find<false>, kFindThreads,
-                                                      sizeof(FindSmem));
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_find_per_sm[1], k_find<true>, kFindThreads,
-                                                      sizeof(FindSmem));
-    for (int k = 0; k < 2; k++)
-        if (g_find_per_sm[k] < 1) g_find_per_sm[k] = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_find<C, DENS>, C::NT, sizeof(FindSmem<C>));
+    if (*per_sm < 1) *per_sm = 1;
     return e;
 }
 
-cudaError_t launch_find(const TreeDev &T, int ngroups, int ngmax, int32_t *nbrs, int32_t *counts,
-                        const float *m, float *smass, float *rho, int sms, cudaStream_t st)
+cudaError_t find_init_attributes()
+{
+    cudaError_t e = find_attr<CfgWide, false>(&g_find_per_sm[0][0]);
+    if (e == cudaSuccess) e = find_attr<CfgWide, true>(&g_find_per_sm[0][1]);
+    if (e == cudaSuccess) e = find_attr<CfgCompact, false>(&g_find_per_sm[1][0]);
+    if (e == cudaSuccess) e = find_attr<CfgCompact, true>(&g_find_per_sm[1][1]);
+    return e;
+}
+
+template <class C>
+static void launch_find_list(const FindArgs &A, int list, int ngroups, int sms, cudaStream_t st)
+{
+    FindArgs B = A;
+    B.list = list;
+    B.ngroups = ngroups;
+    if (ngroups == 0) return;
+    const bool dens = A.rho != nullptr;
+    long long blocks = (long long)sms * g_find_per_sm[list][dens ? 1 : 0];
+    if (ngroups > 0) {
+        const long long nchunks = (ngroups + kFindChunk - 1) / kFindChunk;
+        if (blocks > nchunks) blocks = nchunks;
+    }
+    note_launch();
+    if (dens)
+        k_find<C, true><<<(int)blocks, C::NT, sizeof(FindSmem<C>), st>>>(B);
+    else
+        k_find<C, false><<<(int)blocks, C::NT, sizeof(FindSmem<C>), st>>>(B);
+}
+
+// ngroups / ngroups_c: work units of the wide / compact lists, or -1 to read
+// both counts on the device (graph form: both kernels are launched).
+cudaError_t launch_find(const TreeDev &T, int ngroups, int ngroups_c, int ngmax, int32_t *nbrs,
+                        int32_t *counts, const float *m, float *smass, float *rho, int sms,
+                        cudaStream_t st)
 {
     FindArgs A;
     A.T = T;
@@ -853,27 +900,18 @@ cudaError_t launch_find(const TreeDev &T, int ngroups, int ngmax, int32_t *nbrs,
     A.counts = counts;
     A.smass = smass;
     A.rho = rho;
-    A.ngroups = ngroups;  // < 0: the count is read on the device
-    if (ngroups == 0) return cudaSuccess;
-    const bool dens = rho != nullptr;
-    if (dens) {
+    A.ngroups = 0;
+    A.list = 0;
+    if (ngroups == 0 && ngroups_c == 0) return cudaSuccess;
+    if (rho) {
         int nb = (T.n + 255) / 256;
         if (nb > sms * 8) nb = sms * 8;
         if (nb < 1) nb = 1;
         note_launch();
         k_mass_to_tree<<<nb, 256, 0, st>>>(T.spos, m, smass, T.n);
     }
-    const int per_sm = g_find_per_sm[dens ? 1 : 0];
-    long long blocks = (long long)sms * per_sm;
-    if (ngroups > 0) {
-        const long long nchunks = (ngroups + kFindChunk - 1) / kFindChunk;
-        if (blocks > nchunks) blocks = nchunks;
-    }
-    note_launch();
-    if (dens)
-        k_find<true><<<(int)blocks, kFindThreads, sizeof(FindSmem), st>>>(A);
-    else
-        k_find<false><<<(int)blocks, kFindThreads, sizeof(FindSmem), st>>>(A);
+    launch_find_list<CfgWide>(A, 0, ngroups, sms, st);
+    launch_find_list<CfgCompact>(A, 1, ngroups_c, sms, st);
     return cudaGetLastError();
 }
 
@@ -915,9 +953,9 @@ static cudaError_t noalloc_scratch(float **out)
     return cudaSuccess;
 }
 
-cudaError_t launch_find_density_noalloc(const TreeDev &T, int ngroups, int ngmax, int32_t *nbrs,
-                                        int32_t *counts, const float *m, float *rho, int sms,
-                                        cudaStream_t st)
+cudaError_t launch_find_density_noalloc(const TreeDev &T, int ngroups, int ngroups_c, int ngmax,
+                                        int32_t *nbrs, int32_t *counts, const float *m, float *rho,
+                                        int sms, cudaStream_t st)
 {
     if ((long long)T.n > kNoAllocMaxN) return cudaErrorInvalidValue;
     float *scratch = nullptr;
@@ -925,7 +963,7 @@ cudaError_t launch_find_density_noalloc(const TreeDev &T, int ngroups, int ngmax
     if (e != cudaSuccess) return e;
     // k_mass_to_tree overwrites scratch[0, n) before k_find reads it, so
     // nothing left by an earlier call needs clearing.
-    return launch_find(T, ngroups, ngmax, nbrs, counts, m, scratch, rho, sms, st);
+    return launch_find(T, ngroups, ngroups_c, ngmax, nbrs, counts, m, scratch, rho, sms, st);
 }
 
 // ---------------------------------------------------------------- density

@@ -4,13 +4,14 @@
 
 namespace bt {
 
-cudaError_t launch_find(const TreeDev &T, int ngroups, int ngmax, int32_t *nbrs, int32_t *counts,
-                        const float *m, float *smass, float *rho, int sms, cudaStream_t st);
+cudaError_t launch_find(const TreeDev &T, int ngroups, int ngroups_c, int ngmax, int32_t *nbrs,
+                        int32_t *counts, const float *m, float *smass, float *rho, int sms,
+                        cudaStream_t st);
 cudaError_t launch_density(const TreeDev &T, const float *m, const int32_t *nbrs,
                            const int32_t *counts, int ngmax, float *rho, int sms, cudaStream_t st);
-cudaError_t launch_find_density_noalloc(const TreeDev &T, int ngroups, int ngmax, int32_t *nbrs,
-                                        int32_t *counts, const float *m, float *rho, int sms,
-                                        cudaStream_t st);
+cudaError_t launch_find_density_noalloc(const TreeDev &T, int ngroups, int ngroups_c, int ngmax,
+                                        int32_t *nbrs, int32_t *counts, const float *m, float *rho,
+                                        int sms, cudaStream_t st);
 long long noalloc_max_particles();
 size_t find_smem_bytes();
 cudaError_t find_init_attributes();

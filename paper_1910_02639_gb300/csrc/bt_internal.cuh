@@ -243,6 +243,8 @@ struct Counters {
     int level_go;      // another level follows
     int abort;         // capacity or input problem: the remaining kernels do nothing
     long long hist_need;  // histogram entries a level asked for (on abort)
+    int ngroups_c;     // work units of the compact-shape list (end of the groups array)
+    int pad_c;
 };
 
 // Per big cell of the current level.
@@ -283,6 +285,7 @@ struct SetRec {
 enum : int {
     kSetOctree = 1,    // b fixed to 2 (no Eq. 1 / Eq. 4): the classical octree
     kSetLeafRoot = 2,  // the whole set fits one leaf
+    kSetFindCompact = 4,  // searched by the compact block shape (4 warps, 512 candidates)
 };
 
 // Work units are (first tree position, set << 6 | count), count <= 32.

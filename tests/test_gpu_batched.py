@@ -160,6 +160,8 @@ def test_batched_argument_errors(bt):
 @pytest.mark.parametrize("params", [
     dict(group_size=8), dict(group_size=16), dict(group_size=1),
     dict(bucket_size=64, beta=0.25, group_size=16), dict(bucket_size=8, beta=0.75),
+    dict(find_compact=True), dict(find_compact=True, bucket_size=8, group_size=16),
+    [dict(find_compact=bool(i % 2), bucket_size=(8, 16, 32)[i % 3]) for i in range(10)],
 ])
 def test_tuning_knobs_never_change_results(bt, params):
     # s, beta and the work-unit size change the tree and the schedule only:
@@ -201,7 +203,7 @@ def test_autotuner_table_and_params(bt):
     assert set(table) == {size_class(s.n) for s in sets}
     for e in table.values():
         assert e["bucket_size"] in (8, 16, 32, 64) and e["beta"] in (0.25, 0.5, 0.75)
-        assert e["group_size"] in (16, 32) and e["ms"] > 0
+        assert e["group_size"] in (16, 32) and e["find_compact"] in (False, True) and e["ms"] > 0
     params = tu.params_for(sets)
     _, _, ref = run_batched(bt, sets)
     _, _, got = run_batched(bt, sets, params)
@@ -256,7 +258,8 @@ def test_graph_relaunch_with_new_parameters_and_new_inputs(bt):
         _assert_same(got[i], ref[i], "first launch, set %d" % i)
     # same buffers and sizes: the captured graph is relaunched; per-set
     # parameters are read on the device at each launch
-    for params in (dict(bucket_size=8, beta=0.25), dict(bucket_size=64, group_size=16), None):
+    for params in (dict(bucket_size=8, beta=0.25), dict(bucket_size=64, group_size=16),
+                   dict(find_compact=True), None):
         tree, _, got, bufs = run_graph(bt, sets, params=params, tree=tree, bufs=bufs)
         for i in range(len(sets)):
             _assert_same(got[i], ref[i], "relaunch %s, set %d" % (params, i))
