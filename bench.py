@@ -347,7 +347,7 @@ def run_gpu(args):
 
     # ---- serving: Poisson request stream, continuous batching vs plain
     if not args.no_serving:
-        out["serving"] = run_serving_section(args, dev, rank, ws)
+        out["serving"] = run_serving_section(args, dev, dist, rank, ws)
 
     # ---- end to end through the public API, host buffers
     if not args.no_e2e:
@@ -493,7 +493,7 @@ def run_batched_section(args, bt, dev, stream, dist, rank, ws):
 
 
 # ---------------------------------------------------------------- serving
-def run_serving_section(args, dev, rank, ws):
+def run_serving_section(args, dev, dist, rank, ws):
     """Poisson arrivals (200 requests/s), sizes log-uniform in [1e4, 2e6], the
     three distributions of the batched workload; each request = copy in +
     build + find + density, results left in HBM.  Served by the
@@ -542,13 +542,23 @@ def run_serving_section(args, dev, rank, ws):
     same = all(sums[("served", r.rid)] == sums[("plain", r.rid)] for r in reqs)
     st = serving.latency_stats(served, total)
     sp_ = serving.latency_stats(plain, total)
+    st_sat = serving.latency_stats(sat, total)["pairs_per_s"]
+    sp_sat = serving.latency_stats(plain_sat, total)["pairs_per_s"]
+    if dist:
+        # each rank served its own share of the stream: throughputs add up;
+        # latency percentiles are rank 0's
+        t = torch.tensor([st["pairs_per_s"], sp_["pairs_per_s"], st_sat, sp_sat, float(same == 0)],
+                         dtype=torch.float64, device=dev)
+        dist.all_reduce(t)
+        st["pairs_per_s"], sp_["pairs_per_s"], st_sat, sp_sat = (float(v) for v in t[:4])
+        same = t[4].item() == 0.0
     out = {"workload": f"poisson_{args.serving_requests}_requests_200_per_s",
            "requests": len(reqs), "particles": int(sum(r.n for r in reqs)), "pairs": total,
            "slots": args.serving_slots, "ngmax": ngmax,
            "served": {k: st[k] for k in ("p50_ms", "p99_ms", "mean_ms", "pairs_per_s")},
            "plain": {k: sp_[k] for k in ("p50_ms", "p99_ms", "mean_ms", "pairs_per_s")},
-           "saturated_pairs_per_s": {"served": serving.latency_stats(sat, total)["pairs_per_s"],
-                                     "plain": serving.latency_stats(plain_sat, total)["pairs_per_s"]},
+           "saturated_pairs_per_s": {"served": st_sat, "plain": sp_sat},
+           "ranks": ws,
            "mean_batch_size": float(np.mean([r.batch_size for r in served])),
            "identical_to_plain": bool(same)}
     return out
