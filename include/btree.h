@@ -195,6 +195,29 @@ int btree_find_neighbors(const btree_t *t, int ngmax, int32_t *neighbors,
                          int32_t *counts, void *stream);
 
 /*
+ * btree_find_neighbors_csr -- FindNeighbors (Algorithm 2) into compressed
+ * rows: every neighbour of every particle, no ngmax cap.  The paper has no
+ * output format of its own; this is the compacted form of the same lists.
+ *
+ * Two passes over the tree: the first counts (and, when m != NULL, computes
+ * rho exactly as btree_find_neighbors_density does), an exclusive scan turns
+ * the counts into row offsets, and the second writes row i, ascending by
+ * original index, at neighbors[offsets[i] .. offsets[i+1]).
+ * m, rho    : device float32 [n] or both NULL (no density).
+ * offsets   : device int64 [n + 1], written; offsets[n] = total pairs.
+ * neighbors : device int32 [capacity], or NULL to stop after the offsets
+ *             (e.g. to size the buffer: the total is returned in *total).
+ * capacity  : entries available in neighbors.
+ * total     : host int64 or NULL; receives offsets[n].
+ * Returns BT_ERR_CAPACITY (neighbors untouched, offsets and total valid) when
+ * the total exceeds capacity.  Synchronises `stream` once (to read the
+ * total); the second pass is asynchronous.  Uses scratch owned by the tree
+ * (counts and scan partials, allocated on first use).
+ */
+int btree_find_neighbors_csr(const btree_t *t, const float *m, float *rho, int64_t *offsets,
+                             int32_t *neighbors, int64_t capacity, int64_t *total, void *stream);
+
+/*
  * btree_find_neighbors_density -- FindNeighbors fused with the SPH density.
  *
  * As btree_find_neighbors, and in the same pass

@@ -18,7 +18,7 @@ import threading
 
 __all__ = [
     "BtreeError", "Tree", "btree_build", "btree_build_batched", "btree_build_find_batched",
-    "btree_find_neighbors",
+    "btree_find_neighbors", "btree_find_neighbors_csr",
     "btree_find_neighbors_density", "btree_find_neighbors_density_noalloc",
     "btree_noalloc_max_particles", "sph_density", "btree_status", "btree_get_info",
     "btree_export", "btree_free", "btree_strerror", "btree_version", "btree_kernel_launches",
@@ -81,6 +81,9 @@ def _load():
         lib.btree_build_find_batched.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int, vp,
                                                  ctypes.c_int, vp, vp, vp, vp, vp,
                                                  ctypes.POINTER(vp)]
+        lib.btree_find_neighbors_csr.restype = ctypes.c_int
+        lib.btree_find_neighbors_csr.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int64,
+                                                 ctypes.POINTER(ctypes.c_int64), vp]
         lib.btree_find_neighbors.restype = ctypes.c_int
         lib.btree_find_neighbors.argtypes = [vp, ctypes.c_int, vp, vp, vp]
         lib.btree_find_neighbors_density.restype = ctypes.c_int
@@ -261,6 +264,29 @@ def btree_build_find_batched(x, y, z, h, offsets, ngmax: int, neighbors, counts,
     t.status = st
     t.n = n
     return t
+
+
+def btree_find_neighbors_csr(tree: Tree, offsets, neighbors=None, m=None, rho=None,
+                             stream=None) -> int:
+    """Compressed rows: offsets (int64 [n+1]) always written; rows written
+    into `neighbors` (int32, any size >= the total) when given.  Returns the
+    total number of pairs.  With neighbors=None only the offsets (and the
+    density, when m and rho are given) are computed."""
+    import torch
+    lib = _load()
+    n = tree.n
+    if (m is None) != (rho is None):
+        raise ValueError("give both m and rho, or neither")
+    po = _dptr(offsets, torch.int64, "offsets", n + 1)
+    pm = _dptr(m, torch.float32, "m", n) if m is not None else None
+    pr = _dptr(rho, torch.float32, "rho", n) if rho is not None else None
+    pn = _dptr(neighbors, torch.int32, "neighbors") if neighbors is not None else None
+    cap = int(neighbors.numel()) if neighbors is not None else 0
+    tot = ctypes.c_int64(0)
+    st = lib.btree_find_neighbors_csr(tree.handle, pm, pr, po, pn, cap, ctypes.byref(tot),
+                                      ctypes.c_void_p(_stream_ptr(stream)))
+    _check(st, "btree_find_neighbors_csr")
+    return int(tot.value)
 
 
 def btree_find_neighbors(tree: Tree, ngmax: int, neighbors, counts, stream=None) -> int:

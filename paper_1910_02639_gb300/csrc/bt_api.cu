@@ -76,6 +76,11 @@ struct btree {
     bt_info info{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int64_t hist_need_seen = 0;  // largest level histogram asked for so far
+    // compressed rows: per-particle counts, scan scratch, pinned total
+    int32_t *csr_counts = nullptr;
+    long long *csr_scratch = nullptr;
+    int64_t cap_csr = 0;
+    long long *h_total = nullptr;
     // graph form: private capture streams, the executable graph and its key
     cudaStream_t gs[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t gexec = nullptr;
@@ -132,6 +137,10 @@ void free_all(btree *t)
     for (int k = 0; k < 2; k++) { dev_free(t, t->wpos[k]); dev_free(t, t->wh[k]); dev_free(t, t->big_ids[k]); }
     dev_free(t, t->hist); dev_free(t, t->hoff); dev_free(t, t->cursor); dev_free(t, t->tiles);
     dev_free(t, t->big); dev_free(t, t->small); dev_free(t, t->ctr); dev_free(t, t->smass);
+    dev_free(t, t->csr_counts); dev_free(t, t->csr_scratch);
+    t->csr_counts = nullptr;
+    t->csr_scratch = nullptr;
+    t->cap_csr = 0;
     dev_free(t, t->set_start); dev_free(t, t->set_s); dev_free(t, t->set_na); dev_free(t, t->set_gmax);
     dev_free(t, t->set_flags); dev_free(t, t->set_bbox); dev_free(t, t->set_beta); dev_free(t, t->set_rec);
     t->set_start = t->set_s = t->set_na = t->set_gmax = nullptr;
@@ -593,6 +602,7 @@ static btree *prepare_handle(btree_t **out, const bt_allocator *alloc, void *str
         cudaGetDevice(&t->device);
         cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, t->device);
         if (cudaMallocHost(&t->hctr, sizeof(Counters)) != cudaSuccess ||
+            cudaMallocHost(&t->h_total, sizeof(long long)) != cudaSuccess ||
             cudaEventCreate(&t->ev0) != cudaSuccess || cudaEventCreate(&t->ev1) != cudaSuccess) {
             cudaGetLastError();
             delete t;
@@ -766,6 +776,49 @@ int btree_find_neighbors_density_noalloc(const btree_t *t, const float *m, int n
 
 int64_t btree_noalloc_max_particles(void) { return noalloc_max_particles(); }
 
+int btree_find_neighbors_csr(const btree_t *tc, const float *m, float *rho, int64_t *offsets,
+                             int32_t *neighbors, int64_t capacity, int64_t *total, void *stream)
+{
+    btree *t = const_cast<btree *>(tc);
+    if (!t || !offsets || (m == nullptr) != (rho == nullptr) || capacity < 0) return BT_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t n = t->n;
+    if (n == 0) {
+        cudaMemsetAsync(offsets, 0, sizeof(int64_t), st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return BT_ERR_CUDA;
+        if (total) *total = 0;
+        return BT_OK;
+    }
+    // scratch (allocated on this stream)
+    cudaStream_t keep = t->st;
+    t->st = st;
+    bool ok = true;
+    if (t->cap_csr < n) {
+        ok = realloc_dev(t, t->csr_counts, 0, n, false) &&
+             realloc_dev(t, t->csr_scratch, 0, csr_scratch_elems(n), false);
+        if (ok) t->cap_csr = n;
+    }
+    if (ok && m && t->cap_smass < n) {
+        ok = realloc_dev(t, t->smass, 0, n, false);
+        if (ok) t->cap_smass = n;
+    }
+    t->st = keep;
+    if (!ok) return BT_ERR_OOM;
+    const TreeDev T = view(t);
+    cudaError_t e = launch_find_csr_count(T, t->ngroups, t->ngroups_c, t->csr_counts, m, t->smass, rho,
+                                          reinterpret_cast<long long *>(offsets), t->csr_scratch, t->sms, st);
+    if (e != cudaSuccess) return to_status(e);
+    cudaMemcpyAsync(t->h_total, offsets + n, sizeof(long long), cudaMemcpyDeviceToHost, st);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return to_status(e);
+    const int64_t tot = *t->h_total;
+    if (total) *total = tot;
+    if (!neighbors) return BT_OK;
+    if (tot > capacity) return BT_ERR_CAPACITY;
+    return to_status(launch_find_csr_rows(T, t->ngroups, t->ngroups_c,
+                                          reinterpret_cast<const long long *>(offsets), neighbors,
+                                          t->csr_counts, t->sms, st));
+}
+
 int sph_density(const btree_t *t, const float *m, const int32_t *neighbors, const int32_t *counts,
                 int ngmax, float *rho, void *stream)
 {
@@ -872,6 +925,7 @@ void btree_free(btree_t *t)
         if (t->gs[k]) cudaStreamDestroy(t->gs[k]);
     free_all(t);
     if (t->hctr) cudaFreeHost(t->hctr);
+    if (t->h_total) cudaFreeHost(t->h_total);
     if (t->h_rec) cudaFreeHost(t->h_rec);
     if (t->ev0) cudaEventDestroy(t->ev0);
     if (t->ev1) cudaEventDestroy(t->ev1);

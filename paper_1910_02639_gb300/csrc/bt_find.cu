@@ -94,6 +94,10 @@ struct FindArgs {
     float *rho;
     int ngroups;  // >= 0: work units of this list; < 0: read on the device
     int list;     // 0: the wide-shape list (front of T.groups); 1: the compact list (back)
+    // compressed rows: row i at nbrs + row_off[i], length row_off[i+1] - row_off[i]
+    // (null: fixed rows of ngmax); count_only: counts (and density), no rows
+    const long long *row_off;
+    int count_only;
 };
 
 __device__ __forceinline__ float warp_min(float v)
@@ -543,7 +547,10 @@ __device__ void group_window(const FindArgs &A, FindSmem<C> &S, bool presorted)
         const int total = __shfl_sync(~0u, incl, 31);
         const int excl = incl - cnt;
         const int base = S.qcnt[p];
-        int32_t *row = A.nbrs + (long long)S.qorig[p] * A.ngmax;
+        const long long qo = S.qorig[p];
+        int32_t *row = A.row_off ? A.nbrs + A.row_off[qo] : A.nbrs + qo * A.ngmax;
+        const long long rowcap = A.count_only ? 0
+                                 : (A.row_off ? A.row_off[qo + 1] - A.row_off[qo] : (long long)A.ngmax);
         const float4 P = S.q[p];
         const float inv_h = DENS ? __frcp_rn(S.qh[p]) : 0.0f;
         // lane L takes the list positions congruent to L mod 32 and continues
@@ -579,8 +586,8 @@ __device__ void group_window(const FindArgs &A, FindSmem<C> &S, bool presorted)
                 const uint32_t key2 = two ? S.key[hl[i + 32]] : 0u;
                 const int pos = base + b0 + i;
                 const int vbase = kmin - S.set_lo;
-                if (pos < A.ngmax) row[pos] = vbase + (int)(key1 >> C::SLOT_BITS);
-                if (two && pos + 32 < A.ngmax) row[pos + 32] = vbase + (int)(key2 >> C::SLOT_BITS);
+                if (pos < rowcap) row[pos] = vbase + (int)(key1 >> C::SLOT_BITS);
+                if (two && pos + 32 < rowcap) row[pos + 32] = vbase + (int)(key2 >> C::SLOT_BITS);
                 if (DENS) {
                     const int s1 = key1 & (C::CAP - 1), s2 = key2 & (C::CAP - 1);
                     const float4 Q1 = S.cand[s1];
@@ -818,7 +825,7 @@ __global__ void __launch_bounds__(C::NT, 1024 / C::NT) k_find(FindArgs A)
             if (tid < S.gcount) {
                 const int c = S.qcnt[tid];
                 A.counts[S.qorig[tid]] = c;
-                if (c > A.ngmax) atomicOr(&T.ctr->status, kStNgmax);
+                if (!A.count_only && !A.row_off && c > A.ngmax) atomicOr(&T.ctr->status, kStNgmax);
             }
             if (DENS) {
                 for (int p = warp; p < S.gcount; p += C::WARPS) {
@@ -887,6 +894,9 @@ static void launch_find_list(const FindArgs &A, int list, int ngroups, int sms, 
         k_find<C, false><<<(int)blocks, C::NT, sizeof(FindSmem<C>), st>>>(B);
 }
 
+cudaError_t launch_find_rows(FindArgs A, const TreeDev &T, int ngroups, int ngroups_c, const float *m,
+                             int sms, cudaStream_t st);
+
 // ngroups / ngroups_c: work units of the wide / compact lists, or -1 to read
 // both counts on the device (graph form: both kernels are launched).
 cudaError_t launch_find(const TreeDev &T, int ngroups, int ngroups_c, int ngmax, int32_t *nbrs,
@@ -902,6 +912,17 @@ cudaError_t launch_find(const TreeDev &T, int ngroups, int ngroups_c, int ngmax,
     A.rho = rho;
     A.ngroups = 0;
     A.list = 0;
+    A.row_off = nullptr;
+    A.count_only = 0;
+    return launch_find_rows(A, T, ngroups, ngroups_c, m, sms, st);
+}
+
+cudaError_t launch_find_rows(FindArgs A, const TreeDev &T, int ngroups, int ngroups_c, const float *m,
+                             int sms, cudaStream_t st)
+{
+    // the masses in tree order are written here, then read by k_find
+    float *smass = const_cast<float *>(A.smass);
+    float *rho = A.rho;
     if (ngroups == 0 && ngroups_c == 0) return cudaSuccess;
     if (rho) {
         int nb = (T.n + 255) / 256;
@@ -913,6 +934,137 @@ cudaError_t launch_find(const TreeDev &T, int ngroups, int ngroups_c, int ngmax,
     launch_find_list<CfgWide>(A, 0, ngroups, sms, st);
     launch_find_list<CfgCompact>(A, 1, ngroups_c, sms, st);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- compressed rows
+constexpr int kScan64Tile = 2048;
+
+// Exclusive scan of int32 counts [n] into int64 offsets [n + 1] (three
+// passes: tile sums, one block over the tile sums, per-tile apply).
+__global__ void __launch_bounds__(256) k_scan64_tiles(const int32_t *in, long long n, long long *tsum)
+{
+    __shared__ long long ws[8];
+    const long long t0 = (long long)blockIdx.x * kScan64Tile;
+    long long s = 0;
+    for (long long i = t0 + threadIdx.x; i < min(t0 + kScan64Tile, n); i += blockDim.x) s += in[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(~0u, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int k = 0; k < 8; k++) t += ws[k];
+        tsum[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_scan64_sums(long long *tsum, int ntiles, long long *total)
+{
+    __shared__ long long sh[1024];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < ntiles; base += 1024) {
+        const int i = base + threadIdx.x;
+        const long long v = i < ntiles ? tsum[i] : 0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            const long long a = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += a;
+            __syncthreads();
+        }
+        if (i < ntiles) tsum[i] = carry + sh[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += sh[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(256) k_scan64_apply(const int32_t *in, long long n, const long long *toff,
+                                                      long long *out)
+{
+    // 256 threads x 8 items
+    __shared__ long long ws[8];
+    const long long t0 = (long long)blockIdx.x * kScan64Tile;
+    long long v[8];
+    long long s = 0;
+    for (int k = 0; k < 8; k++) {
+        const long long i = t0 + threadIdx.x * 8 + k;
+        v[k] = i < n ? in[i] : 0;
+        s += v[k];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long a = __shfl_up_sync(~0u, incl, o);
+        if (lane >= o) incl += a;
+    }
+    if (lane == 31) ws[wid] = incl;
+    __syncthreads();
+    long long woff = 0;
+    for (int k = 0; k < wid; k++) woff += ws[k];
+    long long run = toff[blockIdx.x] + woff + incl - s;
+    for (int k = 0; k < 8; k++) {
+        const long long i = t0 + threadIdx.x * 8 + k;
+        if (i < n) out[i] = run;
+        run += v[k];
+    }
+}
+
+__global__ void k_copy_total(const long long *total, long long *dst) { *dst = *total; }
+
+long long csr_scratch_elems(long long n) { return (n + kScan64Tile - 1) / kScan64Tile + 2; }
+
+cudaError_t launch_find_csr_count(const TreeDev &T, int ngroups, int ngroups_c, int32_t *counts,
+                                  const float *m, float *smass, float *rho, long long *offsets,
+                                  long long *scratch, int sms, cudaStream_t st)
+{
+    FindArgs A;
+    A.T = T;
+    A.ngmax = 0;
+    A.nbrs = nullptr;
+    A.counts = counts;
+    A.smass = smass;
+    A.rho = rho;
+    A.ngroups = 0;
+    A.list = 0;
+    A.row_off = nullptr;
+    A.count_only = 1;
+    cudaError_t e = launch_find_rows(A, T, ngroups, ngroups_c, m, sms, st);
+    if (e != cudaSuccess) return e;
+    const long long n = T.n;
+    const int ntiles = (int)((n + kScan64Tile - 1) / kScan64Tile);
+    long long *total = scratch + ntiles;
+    if (ntiles > 0) {
+        note_launch(3);
+        k_scan64_tiles<<<ntiles, 256, 0, st>>>(counts, n, scratch);
+        k_scan64_sums<<<1, 1024, 0, st>>>(scratch, ntiles, total);
+        k_scan64_apply<<<ntiles, 256, 0, st>>>(counts, n, scratch, offsets);
+    } else {
+        cudaMemsetAsync(total, 0, sizeof(long long), st);
+    }
+    note_launch();
+    k_copy_total<<<1, 1, 0, st>>>(total, offsets + n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_find_csr_rows(const TreeDev &T, int ngroups, int ngroups_c, const long long *offsets,
+                                 int32_t *nbrs, int32_t *counts, int sms, cudaStream_t st)
+{
+    FindArgs A;
+    A.T = T;
+    A.ngmax = 0;
+    A.nbrs = nbrs;
+    A.counts = counts;
+    A.smass = nullptr;
+    A.rho = nullptr;
+    A.ngroups = 0;
+    A.list = 0;
+    A.row_off = offsets;
+    A.count_only = 0;
+    return launch_find_rows(A, T, ngroups, ngroups_c, nullptr, sms, st);
 }
 
 // ---------------------------------------------------------------- no-alloc form

@@ -13,6 +13,15 @@ cudaError_t launch_find_density_noalloc(const TreeDev &T, int ngroups, int ngrou
                                         int32_t *nbrs, int32_t *counts, const float *m, float *rho,
                                         int sms, cudaStream_t st);
 long long noalloc_max_particles();
+// Compressed rows: the counting pass (density fused when rho != null) and the
+// exclusive scan into offsets [n + 1]; then the row-writing pass.  scratch:
+// csr_scratch_elems(n) int64.
+long long csr_scratch_elems(long long n);
+cudaError_t launch_find_csr_count(const TreeDev &T, int ngroups, int ngroups_c, int32_t *counts,
+                                  const float *m, float *smass, float *rho, long long *offsets,
+                                  long long *scratch, int sms, cudaStream_t st);
+cudaError_t launch_find_csr_rows(const TreeDev &T, int ngroups, int ngroups_c, const long long *offsets,
+                                 int32_t *nbrs, int32_t *counts, int sms, cudaStream_t st);
 size_t find_smem_bytes();
 cudaError_t find_init_attributes();
 

@@ -304,3 +304,38 @@ def test_graph_form_counts_its_kernels(bt):
     l1 = bt.btree_kernel_launches()
     tree.free()
     assert 20 <= l1 - l0 <= 400
+
+
+# ------------------------------------------------------------------ compressed rows
+def test_csr_rows_are_the_full_lists(bt, oracle):
+    import torch
+    sets = [wl.uniform_cube(6000, seed=527, target=400), wl.plummer(5000, seed=528, target=90)]
+    dev = torch.device("cuda:0")
+    off, *arrs = _concat(sets)
+    x, y, z, h, m = (torch.from_numpy(a).to(dev) for a in arrs)
+    n = int(off[-1])
+    tree = bt.btree_build_batched(x, y, z, h, off, [dict(), dict(find_compact=True)])
+    offsets = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    rho = torch.empty(n, dtype=torch.float32, device=dev)
+    total = bt.btree_find_neighbors_csr(tree, offsets, m=m, rho=rho)  # sizes only
+    nbrs = torch.full((total + 5,), -3, dtype=torch.int32, device=dev)
+    assert bt.btree_find_neighbors_csr(tree, offsets, nbrs) == total
+    with pytest.raises(bt.BtreeError) as ei:
+        bt.btree_find_neighbors_csr(tree, offsets, nbrs[:total - 1])
+    assert ei.value.status == bt.BT_ERR_CAPACITY
+    torch.cuda.synchronize()
+    o = offsets.cpu().numpy()
+    rows = nbrs.cpu().numpy()
+    assert o[0] == 0 and o[-1] == total and np.all(rows[total:] == -3)
+    # fused fixed-row density is the same bits
+    _, _, ref = run_batched(bt, sets, [dict(), dict(find_compact=True)], ngmax=2048)
+    rho_h = rho.cpu().numpy()
+    for i, s in enumerate(sets):
+        a = int(off[i])
+        cnt = np.diff(o[a:a + s.n + 1])
+        ref_nb, ref_cnt = oracle.find_brute(s.x, s.y, s.z, s.h, s.n)  # full rows
+        assert np.array_equal(cnt, ref_cnt), "set %d counts" % i
+        for r in range(s.n):
+            assert np.array_equal(rows[o[a + r]:o[a + r + 1]], ref_nb[r, :ref_cnt[r]]), "set %d row %d" % (i, r)
+        assert np.array_equal(rho_h[a:a + s.n].view(np.int32), ref[i]["rho"].view(np.int32))
+    tree.free()
