@@ -120,9 +120,14 @@ int btree_build(const float *x, const float *y, const float *z, const float *h,
 #define BT_SET_FIND_COMPACT 2 /* search this set with 4 warps per work unit and a
                                  512-candidate window instead of 8 warps and 1024
                                  (often faster on near-uniform sets); same results */
+#define BT_SET_2D 4           /* k = 2 (Table 1: the tree of a two-dimensional
+                                 problem): Eqs. 1 and 4 with b^2, cells split in x
+                                 and y only (b^2 sub-cells), z never split.  The
+                                 neighbour lists are those of the 3-D distance, so
+                                 a planar set (z = 0) gets the 2-D lists. */
 typedef struct {
     int bucket_size; /* s >= 1                                  */
-    int flags;       /* 0 or BT_SET_OCTREE | BT_SET_FIND_COMPACT */
+    int flags;       /* 0 or BT_SET_OCTREE | BT_SET_FIND_COMPACT | BT_SET_2D */
     double alpha;    /* underfull fraction (Eq. 4), e.g. 0.5    */
     double beta;     /* empty-cell limit (Eq. 4), e.g. 0.5      */
     int group_size;  /* queries searched together (a find work

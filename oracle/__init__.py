@@ -17,7 +17,9 @@ Parity status per function (what pins it, see ``tests/test_oracle_pins.py``):
   build             -- ratio loop collapses a clustered cell to b=2 (Sec. 3.1
                        step 3), invariants (each particle in one leaf, boxes tile);
                        octree mode: a 8x8x8 lattice at s=1 is the perfect
-                       depth-3 octree (73 internal cells).
+                       depth-3 octree (73 internal cells); k = 2: closed-form
+                       b^2 s >= n, an 8x8 planar lattice gives the perfect
+                       quadtree (21 internal cells) and z is never split.
   find_brute        -- closed-form lattice counts (92 interior neighbours at
                        h=1.5, strict <), hand-checked tiny sets, pair symmetry.
   find_tree         -- equal to find_brute (the definition) on random sets.
@@ -78,6 +80,10 @@ def _load():
         lib.orc_build.argtypes = [vp, vp, vp, i64, i64, dbl, dbl]
         lib.orc_build2.restype = vp
         lib.orc_build2.argtypes = [vp, vp, vp, i64, i64, dbl, dbl, ctypes.c_int]
+        lib.orc_build_ex.restype = vp
+        lib.orc_build_ex.argtypes = [vp, vp, vp, i64, i64, dbl, dbl, ctypes.c_int, ctypes.c_int]
+        lib.orc_branching_factor2.restype = i64
+        lib.orc_branching_factor2.argtypes = [i64, i64]
         lib.orc_free.restype = None
         lib.orc_free.argtypes = [vp]
         for f in ("orc_num_nodes", "orc_num_slots"):
@@ -113,8 +119,10 @@ def _ptr(a):
 
 
 # ---------------------------------------------------------------- scalars
-def branching_factor(n: int, s: int) -> int:
-    """Eq. 1 in exact integers."""
+def branching_factor(n: int, s: int, k: int = 3) -> int:
+    """Eq. 1 in exact integers (k = 3, or 2 for a two-dimensional tree)."""
+    if k == 2:
+        return int(_load().orc_branching_factor2(n, s))
     return int(_load().orc_branching_factor(n, s))
 
 
@@ -162,13 +170,15 @@ def num_threads() -> int:
 class OracleTree:
     """The oracle's b-tree (Algorithm 1) over float32 positions."""
 
-    def __init__(self, x, y, z, bucket_size=16, alpha=0.5, beta=0.5, octree=False):
+    def __init__(self, x, y, z, bucket_size=16, alpha=0.5, beta=0.5, octree=False, dim=3):
         lib = _load()
         self.x, self.y, self.z = _f32(x), _f32(y), _f32(z)
         self.n = int(self.x.shape[0])
         self.bucket_size = int(bucket_size)
-        self._t = lib.orc_build2(_ptr(self.x), _ptr(self.y), _ptr(self.z), self.n,
-                                 self.bucket_size, float(alpha), float(beta), int(bool(octree)))
+        self.dim = int(dim)
+        self._t = lib.orc_build_ex(_ptr(self.x), _ptr(self.y), _ptr(self.z), self.n,
+                                   self.bucket_size, float(alpha), float(beta), int(bool(octree)),
+                                   self.dim)
         if not self._t:
             raise ValueError("oracle build rejected its arguments")
         self._lib = lib

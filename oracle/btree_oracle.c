@@ -66,6 +66,16 @@ int64_t orc_branching_factor(int64_t n, int64_t s)
     return b;
 }
 
+/* The same for k = 2 (a two-dimensional tree, Table 1): the smallest b >= 2
+ * with b^2 * s >= n. */
+int64_t orc_branching_factor2(int64_t n, int64_t s)
+{
+    int64_t b = 2;
+    while (b * b * s < n)
+        b++;
+    return b;
+}
+
 /* ------------------------------------------------------------------ */
 /* Eq. 2: sub-cell coordinate of one particle in one dimension        */
 /* ------------------------------------------------------------------ */
@@ -154,6 +164,7 @@ typedef struct {
     int64_t n, s;
     double alpha, beta;
     int octree;           /* b fixed to 2 at every split (no Eq. 1 / Eq. 4) */
+    int dim;              /* k = 3, or 2: cells split in x and y only */
     const float *x, *y, *z;
     int64_t *perm;        /* original particle indices in tree order */
     orc_node *nodes;
@@ -208,20 +219,23 @@ static void build_node(orc_tree *t, int64_t ni)
         return;
     }
 
-    /* Step 1: branching factor (Eq. 1); the octree always halves. */
-    int64_t b = t->octree ? 2 : orc_branching_factor(nd.count, t->s);
+    /* Step 1: branching factor (Eq. 1, k = dim); the octree always halves. */
+    int64_t b = t->octree ? 2 : (t->dim == 2 ? orc_branching_factor2(nd.count, t->s)
+                                             : orc_branching_factor(nd.count, t->s));
     int64_t *counts = NULL;
     const double under = t->alpha * (double)t->s;
     for (;;) {
-        /* Step 2: distribute the particles (Eqs. 2-3) and count n_j. */
-        int64_t ncell = b * b * b;
+        /* Step 2: distribute the particles (Eqs. 2-3) and count n_j; with
+         * k = 2 the z coordinate is not split (sub-cell coordinate 0). */
+        int64_t ncell = t->dim == 2 ? b * b : b * b * b;
         counts = (int64_t *)realloc(counts, (size_t)ncell * sizeof(int64_t));
         memset(counts, 0, (size_t)ncell * sizeof(int64_t));
         for (int64_t k = 0; k < nd.count; k++) {
             int64_t p = t->perm[nd.start + k];
             int64_t c[3];
             for (int l = 0; l < 3; l++)
-                c[l] = orc_child_coord(pcoord(t, p, l), nd.lo[l], nd.hi[l], b);
+                c[l] = (t->dim == 2 && l == 2) ? 0
+                                               : orc_child_coord(pcoord(t, p, l), nd.lo[l], nd.hi[l], b);
             int64_t j = orc_child_id(c[0], c[1], c[2], b);
             t->cell[nd.start + k] = j;
             counts[j]++;
@@ -239,12 +253,16 @@ static void build_node(orc_tree *t, int64_t ni)
         }
         break;
     }
-    int64_t ncell = b * b * b;
+    int64_t ncell = t->dim == 2 ? b * b : b * b * b;
 
-    /* Child boxes: equal-size sub-cells of this cell. */
+    /* Child boxes: equal-size sub-cells of this cell (bl sub-cells along
+     * dimension l: b, or 1 for the unsplit z of k = 2). */
+    int64_t bl[3];
     double w[3];
-    for (int l = 0; l < 3; l++)
-        w[l] = (nd.hi[l] - nd.lo[l]) / (double)b;
+    for (int l = 0; l < 3; l++) {
+        bl[l] = (t->dim == 2 && l == 2) ? 1 : b;
+        w[l] = (nd.hi[l] - nd.lo[l]) / (double)bl[l];
+    }
 
     /* No-progress guard: everything in one child whose box is this box. */
     int64_t nonempty = 0, only = -1;
@@ -258,7 +276,7 @@ static void build_node(orc_tree *t, int64_t ni)
         int same = 1;
         for (int l = 0; l < 3; l++) {
             double clo = nd.lo[l] + (double)c[l] * w[l];
-            double chi = (c[l] == b - 1) ? nd.hi[l] : nd.lo[l] + (double)(c[l] + 1) * w[l];
+            double chi = (c[l] == bl[l] - 1) ? nd.hi[l] : nd.lo[l] + (double)(c[l] + 1) * w[l];
             if (clo != nd.lo[l] || chi != nd.hi[l])
                 same = 0;
         }
@@ -293,7 +311,7 @@ static void build_node(orc_tree *t, int64_t ni)
         orc_node *ch = &t->nodes[ci];
         for (int l = 0; l < 3; l++) {
             ch->lo[l] = nd.lo[l] + (double)c[l] * w[l];
-            ch->hi[l] = (c[l] == b - 1) ? nd.hi[l] : nd.lo[l] + (double)(c[l] + 1) * w[l];
+            ch->hi[l] = (c[l] == bl[l] - 1) ? nd.hi[l] : nd.lo[l] + (double)(c[l] + 1) * w[l];
         }
         ch->start = nd.start + offs[j];
         ch->count = counts[j];
@@ -315,13 +333,14 @@ static void build_node(orc_tree *t, int64_t ni)
 /* octree != 0: the classical octree the paper compares with (Sec. 2: b = 2
  * in every dimension at every level; with b = 2 the ratio test of Eq. 4
  * never halves, so the same BuildTree steps apply). */
-orc_tree *orc_build2(const float *x, const float *y, const float *z, int64_t n,
-                     int64_t s, double alpha, double beta, int octree)
+orc_tree *orc_build_ex(const float *x, const float *y, const float *z, int64_t n,
+                       int64_t s, double alpha, double beta, int octree, int dim)
 {
-    if (n < 0 || s < 1)
+    if (n < 0 || s < 1 || (dim != 2 && dim != 3))
         return NULL;
     orc_tree *t = (orc_tree *)calloc(1, sizeof(orc_tree));
     t->octree = octree;
+    t->dim = dim;
     t->n = n;
     t->s = s;
     t->alpha = alpha;
@@ -362,10 +381,16 @@ orc_tree *orc_build2(const float *x, const float *y, const float *z, int64_t n,
     return t;
 }
 
+orc_tree *orc_build2(const float *x, const float *y, const float *z, int64_t n,
+                     int64_t s, double alpha, double beta, int octree)
+{
+    return orc_build_ex(x, y, z, n, s, alpha, beta, octree, 3);
+}
+
 orc_tree *orc_build(const float *x, const float *y, const float *z, int64_t n,
                     int64_t s, double alpha, double beta)
 {
-    return orc_build2(x, y, z, n, s, alpha, beta, 0);
+    return orc_build_ex(x, y, z, n, s, alpha, beta, 0, 3);
 }
 
 void orc_free(orc_tree *t)
@@ -446,8 +471,14 @@ static void walk(const orc_tree *t, int64_t ni, int64_t p, double two_h,
     }
     int64_t b = nd->b;
     int64_t rmin[3], rmax[3];
-    for (int l = 0; l < 3; l++)
+    for (int l = 0; l < 3; l++) {
+        if (t->dim == 2 && l == 2) {  /* k = 2: z is one unsplit sub-cell */
+            rmin[l] = 0;
+            rmax[l] = 0;
+            continue;
+        }
         orc_cell_range(pcoord(t, p, l), two_h, nd->lo[l], nd->hi[l], b, &rmin[l], &rmax[l]);
+    }
     for (int64_t c3 = rmin[2]; c3 <= rmax[2]; c3++)
         for (int64_t c2 = rmin[1]; c2 <= rmax[1]; c2++)
             for (int64_t c1 = rmin[0]; c1 <= rmax[0]; c1++) {

@@ -41,7 +41,8 @@ __device__ __forceinline__ void emit_groups(const TreeDev &T, int set, int start
 __device__ __forceinline__ int set_b0(const TreeDev &T, int set, int count)
 {
     if (T.set_flags[set] & kSetOctree) return 2;
-    return branching_factor(count, T.set_s[set]);
+    return set_dim(T, set) == 2 ? branching_factor2(count, T.set_s[set])
+                                : branching_factor(count, T.set_s[set]);
 }
 
 // ------------------------------------------------------------------ bbox
@@ -163,7 +164,7 @@ __device__ void root_set(TreeDev &T, int s, const LevelBufs &L)
     g.set = s;
     T.geom[s] = g;
     NodeWalk w;
-    make_walk(g, 0, 0, w);
+    make_walk(g, 0, 0, w, set_dim(T, s));
     w.b = 0;  // a leaf until split
     T.walk[s] = w;
     if (n == 0) return;
@@ -248,7 +249,7 @@ __global__ void k_big_setup(TreeDev T, LevelBufs L)
         c.node = node;
         c.b0 = b0;
         c.b = b0;
-        c.hist_n = b0 * b0 * b0;
+        c.hist_n = ncells(b0, set_dim(T, g.set));
         c.chunk_n = (g.count + kBigChunk - 1) / kBigChunk;
         c.hist_base = 0;
         c.chunk_base = 0;
@@ -366,7 +367,7 @@ __device__ __forceinline__ void block_cell_params(const TreeDev &T, const BigCel
     __syncthreads();
     if (threadIdx.x == 0) {
         s_g = T.geom[c.node];
-        make_walk(s_g, c.b, 0, s_w);
+        make_walk(s_g, c.b, 0, s_w, set_dim(T, c.set));
     }
     __syncthreads();
     g = s_g;
@@ -425,7 +426,7 @@ __global__ void __launch_bounds__(256) k_big_count(TreeDev T, LevelBufs L)
             ci = find_cell_by_hist(big, nb, e);
             const BigCell &c = big[ci];
             const int j = e - c.hist_base;
-            if (c.state == 0 && j < c.b * c.b * c.b) {
+            if (c.state == 0 && j < ncells(c.b, set_dim(T, c.set))) {
                 const int v = hist[e];
                 u = v <= T.set_na[c.set];
                 ne = v > 0;
@@ -524,8 +525,9 @@ __global__ void k_big_finish(TreeDev T, LevelBufs L)
 __device__ void finish_cell(const TreeDev &T, BigCell &c, int slot_level_base)
 {
     const int b = c.b;
+    const int k = set_dim(T, c.set);
     const NodeGeom g = T.geom[c.node];
-    for (int l = 0; l < 3; l++) c.w[l] = cell_width(g.lo[l], g.hi[l], b);
+    for (int l = 0; l < 3; l++) c.w[l] = cell_width(g.lo[l], g.hi[l], dim_b(b, k, l));
     bool leaf = false;
     if (c.ne == 1) {
         const int lj = c.lastj;
@@ -533,7 +535,7 @@ __device__ void finish_cell(const TreeDev &T, BigCell &c, int slot_level_base)
         bool same = true;
         for (int l = 0; l < 3; l++) {
             double clo, chi;
-            child_bounds_w(g.lo[l], g.hi[l], c.w[l], b, cc[l], clo, chi);
+            child_bounds_w(g.lo[l], g.hi[l], c.w[l], dim_b(b, k, l), cc[l], clo, chi);
             if (clo != g.lo[l] || chi != g.hi[l]) same = false;
         }
         leaf = same;
@@ -541,7 +543,7 @@ __device__ void finish_cell(const TreeDev &T, BigCell &c, int slot_level_base)
     if (leaf) {
         c.state = 2;
         NodeWalk w;
-        make_walk(g, 0, 0, w);
+        make_walk(g, 0, 0, w, k);
         w.b = 0;
         T.walk[c.node] = w;
         atomicAdd(&T.ctr->noversized, 1);
@@ -551,7 +553,7 @@ __device__ void finish_cell(const TreeDev &T, BigCell &c, int slot_level_base)
     }
     c.slot0 = slot_level_base + c.hist_base;
     NodeWalk w;
-    make_walk(g, b, c.slot0, w);
+    make_walk(g, b, c.slot0, w, k);
     T.walk[c.node] = w;
     atomicMax(&T.ctr->max_depth, g.depth + 1);
 }
@@ -575,8 +577,9 @@ __global__ void __launch_bounds__(256) k_big_emit(TreeDev T, LevelBufs L)
         const BigCell c = big[ci];
         if (c.state != 1) continue;
         const int b = c.b;
+        const int kd = set_dim(T, c.set);
         const int j = e - c.hist_base;
-        if (j >= b * b * b) continue;
+        if (j >= ncells(b, kd)) continue;
         const NodeGeom &g = T.geom[c.node];
         const int s = T.set_s[c.set];
         const int cnt = hist[e];
@@ -593,7 +596,7 @@ __global__ void __launch_bounds__(256) k_big_emit(TreeDev T, LevelBufs L)
                 NodeGeom cg;
                 int cc[3] = {j % b, (j / b) % b, j / (b * b)};
                 for (int l = 0; l < 3; l++)
-                    child_bounds_w(g.lo[l], g.hi[l], c.w[l], b, cc[l], cg.lo[l], cg.hi[l]);
+                    child_bounds_w(g.lo[l], g.hi[l], c.w[l], dim_b(b, kd, l), cc[l], cg.lo[l], cg.hi[l]);
                 cg.start = start;
                 cg.count = cnt;
                 cg.depth = depth;
@@ -815,6 +818,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
         const int s_set = T.set_s[set];
         const int na = T.set_na[set];
         const bool octree = (T.set_flags[set] & kSetOctree) != 0;
+        const int kd = set_dim(T, set);
         const Src &src = item.src == 0 ? src0 : (item.src == 1 ? src1 : srcin);
         for (int k = lane; k < m0; k += 32) {
             float4 r;
@@ -841,12 +845,12 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                 NodeGeom g;
                 for (int l = 0; l < 3; l++) { g.lo[l] = F.lo[l]; g.hi[l] = F.hi[l]; }
                 g.start = base + a; g.count = m; g.depth = F.depth; g.set = set;
-                int b = octree ? 2 : branching_factor(m, s_set);
+                int b = octree ? 2 : (kd == 2 ? branching_factor2(m, s_set) : branching_factor(m, s_set));
                 for (;;) {
-                    if (lane == 0) make_walk(g, b, 0, S.w);
+                    if (lane == 0) make_walk(g, b, 0, S.w, kd);
                     __syncwarp();
                     const NodeWalk w = S.w;
-                    const int ncell = b * b * b;
+                    const int ncell = ncells(b, kd);
                     for (int j = lane; j < ncell; j += 32) S.hist[j] = 0;
                     __syncwarp();
                     for (int k = lane; k < m; k += 32) {
@@ -865,9 +869,9 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                     }
                     break;
                 }
-                const int ncell = b * b * b;
+                const int ncell = ncells(b, kd);
                 if (lane == 0)
-                    for (int l = 0; l < 3; l++) F.w[l] = cell_width(g.lo[l], g.hi[l], b);
+                    for (int l = 0; l < 3; l++) F.w[l] = cell_width(g.lo[l], g.hi[l], dim_b(b, kd, l));
                 __syncwarp();
                 // no-progress guard
                 int ne = 0, lj = -1;
@@ -881,7 +885,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                     bool same = true;
                     for (int l = 0; l < 3; l++) {
                         double clo, chi;
-                        child_bounds_w(g.lo[l], g.hi[l], F.w[l], b, cc[l], clo, chi);
+                        child_bounds_w(g.lo[l], g.hi[l], F.w[l], dim_b(b, kd, l), cc[l], clo, chi);
                         if (clo != g.lo[l] || chi != g.hi[l]) same = false;
                     }
                     leaf = same;
@@ -889,7 +893,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                 if (leaf) {
                     if (lane == 0) {
                         NodeWalk w;
-                        make_walk(g, 0, 0, w);
+                        make_walk(g, 0, 0, w, kd);
                         w.b = 0;
                         T.walk[F.node] = w;
                         atomicAdd(&T.ctr->noversized, 1);
@@ -965,7 +969,8 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                             NodeGeom cg;
                             int cc[3] = {j % b, (j / b) % b, j / (b * b)};
                             for (int l = 0; l < 3; l++)
-                                child_bounds_w(g.lo[l], g.hi[l], F.w[l], b, cc[l], cg.lo[l], cg.hi[l]);
+                                child_bounds_w(g.lo[l], g.hi[l], F.w[l], dim_b(b, kd, l), cc[l], cg.lo[l],
+                                               cg.hi[l]);
                             cg.start = start; cg.count = cnt; cg.depth = depth; cg.set = set;
                             T.geom[child] = cg;
                         }
@@ -980,7 +985,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                 }
                 if (lane == 0) {
                     NodeWalk w;
-                    make_walk(g, b, slot0, w);
+                    make_walk(g, b, slot0, w, kd);
                     T.walk[F.node] = w;
                     atomicMax(&T.ctr->max_depth, F.depth + 1);
                 }
@@ -1002,7 +1007,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                 __syncwarp();
             } else {
                 // ---- descend into the next internal sub-cell
-                const int ncell = F.b * F.b * F.b;
+                const int ncell = ncells(F.b, kd);
                 int found = -1;
                 while (F.next < ncell && found < 0) {
                     int j = F.next + lane;
@@ -1025,7 +1030,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                     const int b = F.b;
                     int cc[3] = {found % b, (found / b) % b, found / (b * b)};
                     for (int l = 0; l < 3; l++)
-                        child_bounds_w(F.lo[l], F.hi[l], F.w[l], b, cc[l], C.lo[l], C.hi[l]);
+                        child_bounds_w(F.lo[l], F.hi[l], F.w[l], dim_b(b, kd, l), cc[l], C.lo[l], C.hi[l]);
                     C.a = s.start - base; C.m = s.count; C.node = s.child; C.depth = F.depth + 1;
                     C.b = 0; C.slot0 = 0; C.next = 0;
                     C.emit = F.emit && s.count > kWholeMax;

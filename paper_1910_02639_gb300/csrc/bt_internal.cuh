@@ -132,7 +132,9 @@ __device__ __forceinline__ void walk_range(float ql, float qh, const NodeWalk &w
 }
 
 // Fill the walk/coordinate parameters of a node with branching factor b.
-__device__ __forceinline__ void make_walk(const NodeGeom &g, int b, int slot0, NodeWalk &w)
+// k = 2: the z dimension is not split (treated like a zero-width dimension:
+// sub-cell coordinate 0, walk range [0, 0]).
+__device__ __forceinline__ void make_walk(const NodeGeom &g, int b, int slot0, NodeWalk &w, int k = 3)
 {
     w.b = b;
     w.slot0 = slot0;
@@ -143,7 +145,7 @@ __device__ __forceinline__ void make_walk(const NodeGeom &g, int b, int slot0, N
     for (int l = 0; l < 3; l++) {
         double width = __dsub_rn(g.hi[l], g.lo[l]);
         w.lo[l] = __double2float_rn(g.lo[l]);
-        if (width == 0.0) {
+        if (width == 0.0 || (k == 2 && l == 2)) {
             w.flags |= (kFlagDegen0 << l);
             w.scale[l] = 0.0f;
             w.cn[l] = 0.0f;
@@ -207,6 +209,22 @@ __device__ __host__ __forceinline__ int branching_factor(long long n, long long 
     while (b * b * b * s < n) b++;
     return (int)b;
 }
+
+// Eq. 1 for k = 2: smallest b >= 2 with b^2 s >= n.
+__device__ __host__ __forceinline__ int branching_factor2(long long n, long long s)
+{
+    long long b = (long long)sqrtf((float)n / (float)s);
+    if (b < 2) b = 2;
+    while (b > 2 && (b - 1) * (b - 1) * s >= n) b--;
+    while (b * b * s < n) b++;
+    return (int)b;
+}
+
+// Sub-cells of a node: b^k.
+__device__ __host__ __forceinline__ int ncells(int b, int k) { return k == 2 ? b * b : b * b * b; }
+
+// Branching factor of dimension l of a node: b, except the unsplit z of k = 2.
+__device__ __host__ __forceinline__ int dim_b(int b, int k, int l) { return (k == 2 && l == 2) ? 1 : b; }
 
 // Order-preserving float <-> int map for atomicMin/atomicMax on floats.
 __device__ __forceinline__ int float_to_ordered(float f)
@@ -286,6 +304,7 @@ enum : int {
     kSetOctree = 1,    // b fixed to 2 (no Eq. 1 / Eq. 4): the classical octree
     kSetLeafRoot = 2,  // the whole set fits one leaf
     kSetFindCompact = 4,  // searched by the compact block shape (4 warps, 512 candidates)
+    kSetTwoD = 8,         // k = 2: cells split in x and y only (b^2 sub-cells)
 };
 
 // Work units are (first tree position, set << 6 | count), count <= 32.
@@ -317,10 +336,15 @@ struct TreeDev {
 };
 
 // Ratio test of Eq. 4 for a cell of the given set: halve b iff
-// u > beta * b^3, in binary64 (b^3 is exact; u is an integer).
+// u > beta * b^k, in binary64 (b^k is exact; u is an integer).
+__device__ __forceinline__ int set_dim(const TreeDev &T, int set)
+{
+    return (T.set_flags[set] & kSetTwoD) ? 2 : 3;
+}
+
 __device__ __forceinline__ bool ratio_halves(const TreeDev &T, int set, int u, int b)
 {
-    const double bb = (double)(b * b * b);
+    const double bb = (double)ncells(b, set_dim(T, set));
     return (double)u > __dmul_rn(T.set_beta[set], bb);
 }
 

@@ -34,18 +34,18 @@ def run_gpu(s, bucket_size=16, ngmax=256, alpha=0.5, beta=0.5, density=False, tr
     return out
 
 
-def canonical_tree_gpu(e, n, root=0, off=0):
+def canonical_tree_gpu(e, n, root=0, off=0, k=3):
     """Per-internal-cell table and per-particle (cell, sub-cell id) from the
     GPU export; `root` is the set's root node, `off` its first particle."""
     return _canon(e["lo"], e["hi"], e["depth"], e["b"], e["count"],
-                  lambda i: _gpu_children(e, i, off), n, root)
+                  lambda i: _gpu_children(e, i, off, k), n, root)
 
 
-def _gpu_children(e, i, off=0):
+def _gpu_children(e, i, off=0, k=3):
     b = int(e["b"][i])
     k0 = int(e["slot0"][i])
     out = []
-    for j in range(b ** 3):
+    for j in range(b ** k):
         c = int(e["slot_child"][k0 + j])
         st, ct = int(e["slot_start"][k0 + j]), int(e["slot_count"][k0 + j])
         if c >= 0 and int(e["b"][c]) > 0:
@@ -55,16 +55,16 @@ def _gpu_children(e, i, off=0):
     return out
 
 
-def canonical_tree_oracle(e, n):
+def canonical_tree_oracle(e, n, k=3):
     return _canon(e["lo"], e["hi"], e["depth"], e["b"], e["count"],
-                  lambda i: _orc_children(e, i), n)
+                  lambda i: _orc_children(e, i, k), n)
 
 
-def _orc_children(e, i):
+def _orc_children(e, i, k=3):
     b = int(e["b"][i])
     k0 = int(e["slot0"][i])
     out = []
-    for j in range(b ** 3):
+    for j in range(b ** k):
         c = int(e["child"][k0 + j])
         if int(e["b"][c]) > 0:
             out.append((j, ("node", c)))
@@ -105,9 +105,9 @@ def _canon(lo, hi, depth, b, count, children, n, root=0):
     return cells, pcell, pj, keys
 
 
-def compare_trees(gpu_export, orc_export, n, root=0, off=0):
-    gc, gp, gj, gk = canonical_tree_gpu(gpu_export, n, root, off)
-    oc, op_, oj, ok = canonical_tree_oracle(orc_export, n)
+def compare_trees(gpu_export, orc_export, n, root=0, off=0, k=3):
+    gc, gp, gj, gk = canonical_tree_gpu(gpu_export, n, root, off, k)
+    oc, op_, oj, ok = canonical_tree_oracle(orc_export, n, k)
     assert gc == oc, "internal cells (depth, box, b, count) differ"
     # map cell indices through their keys
     gkey = np.array([hash(k) for k in gk] + [0], dtype=np.int64)

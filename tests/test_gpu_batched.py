@@ -339,3 +339,36 @@ def test_csr_rows_are_the_full_lists(bt, oracle):
             assert np.array_equal(rows[o[a + r]:o[a + r + 1]], ref_nb[r, :ref_cnt[r]]), "set %d row %d" % (i, r)
         assert np.array_equal(rho_h[a:a + s.n].view(np.int32), ref[i]["rho"].view(np.int32))
     tree.free()
+
+
+# ------------------------------------------------------------------ k = 2
+def _planar(n, seed, target):
+    rng = np.random.default_rng(seed)
+    x, y = rng.random((2, n)).astype(np.float32)
+    # 2-D number density n per unit area: h from pi (2h)^2 n = target
+    h = np.full(n, np.sqrt(target / (np.pi * n)) / 2, np.float32)
+    return wl._pack(x, y, np.zeros(n, np.float32), h, name="planar")
+
+
+def test_k2_sets_trees_and_lists(bt, oracle):
+    sets = [_planar(20_000, 530, 40), _planar(3_000, 531, 25), wl.uniform_cube(8_000, seed=532, target=60),
+            wl.plummer(4_000, seed=533, target=50), _planar(17, 534, 5)]
+    params = [dict(dim=2), dict(dim=2, octree=True), dict(dim=2, bucket_size=8),
+              dict(dim=2, find_compact=True), dict(dim=2)]
+    tree, off, res = run_batched(bt, sets, params, ngmax=512)
+    e = bt.btree_export(tree)
+    tree.free()
+    for i, (s, p) in enumerate(zip(sets, params)):
+        ot = oracle.OracleTree(s.x, s.y, s.z, bucket_size=p.get("bucket_size", 16),
+                               octree=p.get("octree", False), dim=2)
+        compare_trees(e, ot.export(), s.n, root=i, off=int(off[i]), k=2)
+        ref_nb, ref_cnt = oracle.find_brute(s.x, s.y, s.z, s.h, 512)
+        assert np.array_equal(res[i]["cnt"], ref_cnt), "set %d counts" % i
+        used = np.arange(512)[None, :] < np.minimum(ref_cnt, 512)[:, None]
+        assert np.array_equal(np.where(used, ref_nb, -1), res[i]["nb"]), "set %d lists" % i
+        rho = ot.density(s.h, s.m)
+        assert (np.abs(res[i]["rho"] - rho) / rho).max() < 1e-5, "set %d density" % i
+    # the 2-D trees give the same lists and densities as the 3-D trees
+    _, _, res3 = run_batched(bt, sets, None, ngmax=512)
+    for i in range(len(sets)):
+        _assert_same(res[i], res3[i], "set %d k=2 vs k=3" % i)

@@ -122,7 +122,7 @@ def test_beta_one_never_halves_and_beta_zero_always_halves(oracle):
 
 
 # --------------------------------------------------------------- tree invariants
-def _check_tree_invariants(e, n, s):
+def _check_tree_invariants(e, n, s, k=3):
     leaf = e["b"] == 0
     # every particle in exactly one leaf
     seen = np.zeros(n, np.int64)
@@ -135,7 +135,7 @@ def _check_tree_invariants(e, n, s):
     # children tile the parent: counts add up, boxes inside the parent box
     for i in np.nonzero(~leaf)[0]:
         b = int(e["b"][i])
-        ch = e["child"][e["slot0"][i]:e["slot0"][i] + b ** 3]
+        ch = e["child"][e["slot0"][i]:e["slot0"][i] + b ** k]
         assert e["count"][ch].sum() == e["count"][i]
         assert np.all(e["lo"][ch] >= e["lo"][i]) and np.all(e["hi"][ch] <= e["hi"][i])
         assert np.all(e["depth"][ch] == e["depth"][i] + 1)
@@ -380,3 +380,58 @@ def test_octree_and_btree_give_the_same_lists(oracle):
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     _check_tree_invariants(oracle.OracleTree(s.x, s.y, s.z, bucket_size=8, octree=True).export(),
                            s.n, 8)
+
+
+# --------------------------------------------------------------- k = 2 trees
+@pytest.mark.parametrize("s_", [1, 3, 4, 16])
+def test_branching_factor_k2_closed_form(oracle, s_):
+    for n in list(range(s_ + 1, 400)) + [10**6, 10**6 + 1, 123457]:
+        b = oracle.branching_factor(n, s_, k=2)
+        assert b >= 2 and b * b * s_ >= n
+        assert b == 2 or (b - 1) ** 2 * s_ < n
+    assert oracle.branching_factor(100, 1, k=2) == 10
+    assert oracle.branching_factor(101, 1, k=2) == 11
+
+
+def _planar_lattice(nx, ny):
+    i = np.arange(nx * ny)
+    x, y = (i % nx).astype(np.float32), (i // nx).astype(np.float32)
+    return x, y, np.zeros_like(x), np.full(x.size, 0.75, np.float32)
+
+
+def test_k2_perfect_quadtree_on_a_planar_lattice(oracle):
+    # 8x8 lattice, box [0,7]^2, s = 1, b forced to 2: every split halves x
+    # and y at the middle -> depth 3, 1 + 4 + 16 internal cells, 64 leaves of one
+    x, y, z, h = _planar_lattice(8, 8)
+    t = oracle.OracleTree(x, y, z, bucket_size=1, octree=True, dim=2)
+    e = t.export()
+    internal = e["b"] > 0
+    assert internal.sum() == 21 and t.max_depth == 3
+    assert np.all(e["count"][~internal] <= 1)
+    assert e["count"][~internal].sum() == 64 and np.sum(e["count"][~internal] == 1) == 64
+    _check_tree_invariants(e, 64, 1, k=2)
+    # the b-tree: b0 = 8 (8^2 * 1 >= 64), one level of 64 single-particle cells
+    tb = oracle.OracleTree(x, y, z, bucket_size=1, dim=2)
+    eb = tb.export()
+    assert eb["b"][0] == 8 and tb.max_depth == 1 and (eb["b"] > 0).sum() == 1
+
+
+def test_k2_tree_never_splits_z_and_lists_are_the_definition(oracle):
+    s = wl.uniform_cube(4000, seed=31, target=40)
+    t = oracle.OracleTree(s.x, s.y, s.z, bucket_size=8, dim=2)
+    e = t.export()
+    _check_tree_invariants(e, s.n, 8, k=2)
+    assert np.all(e["lo"][:, 2] == e["lo"][0, 2]) and np.all(e["hi"][:, 2] == e["hi"][0, 2])
+    nb, cnt = t.find(s.h, 128)
+    rnb, rcnt = oracle.find_brute(s.x, s.y, s.z, s.h, 128)
+    assert np.array_equal(cnt, rcnt) and np.array_equal(nb, rnb)
+    # a planar set: the 2-D lists
+    x, y, z, h = _planar_lattice(30, 20)
+    t2 = oracle.OracleTree(x, y, z, bucket_size=4, dim=2)
+    nb2, cnt2 = t2.find(h, 32)
+    rnb2, rcnt2 = oracle.find_brute(x, y, z, h, 32)
+    assert np.array_equal(cnt2, rcnt2) and np.array_equal(nb2, rnb2)
+    # interior points of the unit lattice with h = 0.75: |v|^2 < 2.25 gives
+    # the 8 points at distance 1 and sqrt(2)
+    interior = (x >= 2) & (x <= 27) & (y >= 2) & (y <= 17)
+    assert np.all(cnt2[interior] == 8)
