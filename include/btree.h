@@ -223,6 +223,24 @@ int btree_find_neighbors_csr(const btree_t *t, const float *m, float *rho, int64
                              int32_t *neighbors, int64_t capacity, int64_t *total, void *stream);
 
 /*
+ * btree_pack_rows -- pack fixed rows (from btree_find_neighbors or
+ * btree_find_neighbors_density on this tree) into compressed rows: row i's
+ * first min(counts[i], ngmax) entries go to csr[offsets[i] ..].  The paper
+ * has no counterpart; this is a layout change of the same lists (for moving
+ * only the neighbours, e.g. to the host).  When no count exceeds ngmax the
+ * result equals btree_find_neighbors_csr, at the cost of one read and one
+ * write of the lists instead of a second search.
+ * rows      : device int32 [n * ngmax];  counts : device int32 [n].
+ * offsets   : device int64 [n + 1], written (exclusive scan of the capped counts).
+ * csr       : device int32 [capacity], or NULL to stop after the offsets.
+ * total     : host int64 or NULL; receives offsets[n].
+ * Returns BT_ERR_CAPACITY (csr untouched) when the total exceeds capacity.
+ * Synchronises `stream` once (to read the total); the packing is asynchronous.
+ */
+int btree_pack_rows(const btree_t *t, const int32_t *rows, const int32_t *counts, int ngmax,
+                    int64_t *offsets, int32_t *csr, int64_t capacity, int64_t *total, void *stream);
+
+/*
  * btree_find_neighbors_density -- FindNeighbors fused with the SPH density.
  *
  * As btree_find_neighbors, and in the same pass

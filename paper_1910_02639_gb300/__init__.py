@@ -18,7 +18,7 @@ import threading
 
 __all__ = [
     "BtreeError", "Tree", "btree_build", "btree_build_batched", "btree_build_find_batched",
-    "btree_find_neighbors", "btree_find_neighbors_csr",
+    "btree_find_neighbors", "btree_find_neighbors_csr", "btree_pack_rows",
     "btree_find_neighbors_density", "btree_find_neighbors_density_noalloc",
     "btree_noalloc_max_particles", "sph_density", "btree_status", "btree_get_info",
     "btree_export", "btree_free", "btree_strerror", "btree_version", "btree_kernel_launches",
@@ -84,6 +84,9 @@ def _load():
         lib.btree_find_neighbors_csr.restype = ctypes.c_int
         lib.btree_find_neighbors_csr.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int64,
                                                  ctypes.POINTER(ctypes.c_int64), vp]
+        lib.btree_pack_rows.restype = ctypes.c_int
+        lib.btree_pack_rows.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp, ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_int64), vp]
         lib.btree_find_neighbors.restype = ctypes.c_int
         lib.btree_find_neighbors.argtypes = [vp, ctypes.c_int, vp, vp, vp]
         lib.btree_find_neighbors_density.restype = ctypes.c_int
@@ -288,6 +291,23 @@ def btree_find_neighbors_csr(tree: Tree, offsets, neighbors=None, m=None, rho=No
     st = lib.btree_find_neighbors_csr(tree.handle, pm, pr, po, pn, cap, ctypes.byref(tot),
                                       ctypes.c_void_p(_stream_ptr(stream)))
     _check(st, "btree_find_neighbors_csr")
+    return int(tot.value)
+
+
+def btree_pack_rows(tree: Tree, rows, counts, ngmax: int, offsets, csr=None, stream=None) -> int:
+    """Pack fixed rows into compressed rows; returns the total entries."""
+    import torch
+    lib = _load()
+    n = tree.n
+    pr = _dptr(rows, torch.int32, "rows", n * ngmax)
+    pc = _dptr(counts, torch.int32, "counts", n)
+    po = _dptr(offsets, torch.int64, "offsets", n + 1)
+    pcsr = _dptr(csr, torch.int32, "csr") if csr is not None else None
+    cap = int(csr.numel()) if csr is not None else 0
+    tot = ctypes.c_int64(0)
+    st = lib.btree_pack_rows(tree.handle, pr, pc, int(ngmax), po, pcsr, cap, ctypes.byref(tot),
+                             ctypes.c_void_p(_stream_ptr(stream)))
+    _check(st, "btree_pack_rows")
     return int(tot.value)
 
 

@@ -27,6 +27,7 @@ void note_launch(int k)
 struct GraphKey {
     TreeDev T;
     LevelBufs L;
+    const SetRec *rec;  // mapped staging of the per-set records
     const float *m;
     float *smass, *rho;
     int32_t *nbrs, *counts;
@@ -62,15 +63,17 @@ struct btree {
     int *big_ids[2] = {nullptr, nullptr};
     SmallItem *small = nullptr;
     Counters *ctr = nullptr;
-    Counters *hctr = nullptr;  // pinned host mirror
+    Counters *hctr = nullptr;  // = &rb->c: the host's copy of the counters
+    Readback *rb = nullptr;    // mapped pinned host memory ...
+    Readback *rb_dev = nullptr;  // ... and its device address
     float *smass = nullptr;
     // per-set tables (device) and their pinned host staging
     int nsets = 0, cap_sets = 0;
     int *set_start = nullptr, *set_s = nullptr, *set_na = nullptr, *set_gmax = nullptr;
     int *set_flags = nullptr, *set_bbox = nullptr;
     double *set_beta = nullptr;
-    SetRec *set_rec = nullptr;  // device copy of the staged records
-    SetRec *h_rec = nullptr;    // [cap_sets] pinned staging
+    SetRec *h_rec = nullptr;    // [cap_sets] mapped pinned staging, read by k_init_sets
+    SetRec *h_rec_dev = nullptr;
 
     int ngroups = 0, ngroups_c = 0;  // work units of the wide / compact lists
     bt_info info{};
@@ -80,7 +83,7 @@ struct btree {
     int32_t *csr_counts = nullptr;
     long long *csr_scratch = nullptr;
     int64_t cap_csr = 0;
-    long long *h_total = nullptr;
+
     // graph form: private capture streams, the executable graph and its key
     cudaStream_t gs[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t gexec = nullptr;
@@ -142,11 +145,10 @@ void free_all(btree *t)
     t->csr_scratch = nullptr;
     t->cap_csr = 0;
     dev_free(t, t->set_start); dev_free(t, t->set_s); dev_free(t, t->set_na); dev_free(t, t->set_gmax);
-    dev_free(t, t->set_flags); dev_free(t, t->set_bbox); dev_free(t, t->set_beta); dev_free(t, t->set_rec);
+    dev_free(t, t->set_flags); dev_free(t, t->set_bbox); dev_free(t, t->set_beta);
     t->set_start = t->set_s = t->set_na = t->set_gmax = nullptr;
     t->set_flags = t->set_bbox = nullptr;
     t->set_beta = nullptr;
-    t->set_rec = nullptr;
     t->cap_sets = 0;
     t->geom = nullptr; t->walk = nullptr; t->slots = nullptr; t->groups = nullptr;
     t->spos = nullptr; t->sh = nullptr; t->inv = nullptr;
@@ -262,13 +264,14 @@ int ensure_set_caps(btree *t, int nsets)
     const int c = std::max(nsets, 1);
     if (!realloc_dev(t, t->set_start, 0, c + 1, false) || !realloc_dev(t, t->set_s, 0, c, false) ||
         !realloc_dev(t, t->set_na, 0, c, false) || !realloc_dev(t, t->set_gmax, 0, c, false) ||
-        !realloc_dev(t, t->set_beta, 0, c, false) || !realloc_dev(t, t->set_rec, 0, c, false) ||
+        !realloc_dev(t, t->set_beta, 0, c, false) ||
         !realloc_dev(t, t->set_flags, 0, c, false) || !realloc_dev(t, t->set_bbox, 0, 6 * c, false))
         return BT_ERR_OOM;
     // the previous build has finished reading the staging (builds end synchronised)
     if (t->h_rec) cudaFreeHost(t->h_rec);
     t->h_rec = nullptr;
-    if (cudaMallocHost(&t->h_rec, sizeof(SetRec) * (size_t)c) != cudaSuccess) {
+    if (cudaHostAlloc(&t->h_rec, sizeof(SetRec) * (size_t)c, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(&t->h_rec_dev, t->h_rec, 0) != cudaSuccess) {
         cudaGetLastError();
         return BT_ERR_OOM;
     }
@@ -278,7 +281,7 @@ int ensure_set_caps(btree *t, int nsets)
 
 int read_counters(btree *t, cudaStream_t st)
 {
-    cudaMemcpyAsync(t->hctr, t->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
+    launch_readback(t->ctr, t->cap_nodes > 0 ? t->walk : nullptr, t->rb_dev, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return to_status(e);
     return to_status(cudaGetLastError());
@@ -320,9 +323,8 @@ void record_event(cudaEvent_t ev, cudaStream_t st, bool capture)
 void launch_build_head(btree *t, const TreeDev &T, const LevelBufs &L, cudaStream_t st,
                        bool capture = false)
 {
-    cudaMemcpyAsync(t->set_rec, t->h_rec, sizeof(SetRec) * (size_t)t->nsets, cudaMemcpyHostToDevice, st);
     launch_init_counters(t->ctr, t->nsets, st);
-    launch_init_sets(T, t->set_rec, t->set_start, t->set_s, t->set_na, t->set_beta, t->set_gmax, st);
+    launch_init_sets(T, t->h_rec_dev, t->set_start, t->set_s, t->set_na, t->set_beta, t->set_gmax, st);
     record_event(t->ev0, st, capture);
     launch_bbox(T, L.in.x, L.in.y, L.in.z, L.in.h, t->sms, st);
     launch_roots(T, L, t->sms, st);
@@ -339,10 +341,6 @@ int finish_build(btree *t, cudaStream_t st)
     }
     t->ngroups = c.ngroups;
     t->ngroups_c = c.ngroups_c;
-    NodeWalk w0;
-    w0.b = 0;
-    if (t->nsets > 0) cudaMemcpyAsync(&w0, t->walk, sizeof(NodeWalk), cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return BT_ERR_CUDA;
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, t->ev0, t->ev1) != cudaSuccess) {
         cudaGetLastError();
@@ -355,7 +353,7 @@ int finish_build(btree *t, cudaStream_t st)
     I.num_nodes = c.nnodes;
     I.num_slots = c.nslots;
     I.num_groups = c.ngroups + c.ngroups_c;
-    I.root_b = w0.b;
+    I.root_b = t->rb->root_b;
     I.num_oversized = c.noversized;
     I.build_ms = ms;
     return (c.status & kStOversized) ? BT_WARN_OVERSIZED_LEAF : BT_OK;
@@ -498,6 +496,7 @@ int run_graph_step(btree *t, const float *x, const float *y, const float *z, con
     std::memset(&K, 0, sizeof(K));
     K.T = view(t);
     K.L = lview(t, x, y, z, h);
+    K.rec = t->h_rec_dev;
     K.m = m;
     K.smass = m ? t->smass : nullptr;
     K.rho = rho;
@@ -601,14 +600,15 @@ static btree *prepare_handle(btree_t **out, const bt_allocator *alloc, void *str
         fresh = true;
         cudaGetDevice(&t->device);
         cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, t->device);
-        if (cudaMallocHost(&t->hctr, sizeof(Counters)) != cudaSuccess ||
-            cudaMallocHost(&t->h_total, sizeof(long long)) != cudaSuccess ||
+        if (cudaHostAlloc(&t->rb, sizeof(Readback), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer(&t->rb_dev, t->rb, 0) != cudaSuccess ||
             cudaEventCreate(&t->ev0) != cudaSuccess || cudaEventCreate(&t->ev1) != cudaSuccess) {
             cudaGetLastError();
             delete t;
             *rc = BT_ERR_CUDA;
             return nullptr;
         }
+        t->hctr = &t->rb->c;
         *out = t;
     }
     if (alloc) {
@@ -777,6 +777,40 @@ int btree_find_neighbors_density_noalloc(const btree_t *t, const float *m, int n
 
 int64_t btree_noalloc_max_particles(void) { return noalloc_max_particles(); }
 
+int btree_pack_rows(const btree_t *tc, const int32_t *rows, const int32_t *counts, int ngmax,
+                    int64_t *offsets, int32_t *csr, int64_t capacity, int64_t *total, void *stream)
+{
+    btree *t = const_cast<btree *>(tc);
+    if (!t || ngmax < 1 || !offsets || capacity < 0 || (t->n > 0 && (!rows || !counts))) return BT_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t n = t->n;
+    if (n == 0) {
+        cudaMemsetAsync(offsets, 0, sizeof(int64_t), st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return BT_ERR_CUDA;
+        if (total) *total = 0;
+        return BT_OK;
+    }
+    if (t->cap_csr < n) {
+        cudaStream_t keep = t->st;
+        t->st = st;
+        const bool ok = realloc_dev(t, t->csr_counts, 0, n, false) &&
+                        realloc_dev(t, t->csr_scratch, 0, csr_scratch_elems(n), false);
+        t->st = keep;
+        if (!ok) return BT_ERR_OOM;
+        t->cap_csr = n;
+    }
+    launch_scan64(counts, n, ngmax, reinterpret_cast<long long *>(offsets), t->csr_scratch, st);
+    launch_readback_total(reinterpret_cast<const long long *>(offsets + n), t->rb_dev, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return to_status(e);
+    const int64_t tot = t->rb->total;
+    if (total) *total = tot;
+    if (!csr) return BT_OK;
+    if (tot > capacity) return BT_ERR_CAPACITY;
+    launch_pack_rows(rows, counts, n, ngmax, reinterpret_cast<const long long *>(offsets), csr, t->sms, st);
+    return to_status(cudaGetLastError());
+}
+
 int btree_find_neighbors_csr(const btree_t *tc, const float *m, float *rho, int64_t *offsets,
                              int32_t *neighbors, int64_t capacity, int64_t *total, void *stream)
 {
@@ -809,9 +843,9 @@ int btree_find_neighbors_csr(const btree_t *tc, const float *m, float *rho, int6
     cudaError_t e = launch_find_csr_count(T, t->ngroups, t->ngroups_c, t->csr_counts, m, t->smass, rho,
                                           reinterpret_cast<long long *>(offsets), t->csr_scratch, t->sms, st);
     if (e != cudaSuccess) return to_status(e);
-    cudaMemcpyAsync(t->h_total, offsets + n, sizeof(long long), cudaMemcpyDeviceToHost, st);
+    launch_readback_total(reinterpret_cast<const long long *>(offsets + n), t->rb_dev, st);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return to_status(e);
-    const int64_t tot = *t->h_total;
+    const int64_t tot = t->rb->total;
     if (total) *total = tot;
     if (!neighbors) return BT_OK;
     if (tot > capacity) return BT_ERR_CAPACITY;
@@ -925,8 +959,7 @@ void btree_free(btree_t *t)
     for (int k = 0; k < 3; k++)
         if (t->gs[k]) cudaStreamDestroy(t->gs[k]);
     free_all(t);
-    if (t->hctr) cudaFreeHost(t->hctr);
-    if (t->h_total) cudaFreeHost(t->h_total);
+    if (t->rb) cudaFreeHost(t->rb);
     if (t->h_rec) cudaFreeHost(t->h_rec);
     if (t->ev0) cudaEventDestroy(t->ev0);
     if (t->ev1) cudaEventDestroy(t->ev1);

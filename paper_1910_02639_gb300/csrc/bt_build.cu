@@ -1161,6 +1161,31 @@ cudaError_t build_init_attributes()
                                 (int)small_smem_bytes());
 }
 
+// One thread: copy the counters (and node 0's b) into the mapped host mirror.
+__global__ void k_readback(const Counters *__restrict__ ctr, const NodeWalk *__restrict__ walk0,
+                           Readback *out)
+{
+    out->c = *ctr;
+    out->root_b = walk0 ? walk0->b : 0;
+    __threadfence_system();
+}
+
+__global__ void k_readback_total(const long long *__restrict__ total, Readback *out)
+{
+    out->total = *total;
+    __threadfence_system();
+}
+
+void launch_readback(const Counters *ctr, const NodeWalk *walk0, Readback *out, cudaStream_t st)
+{
+    k_readback<<<1, 1, 0, st>>>(ctr, walk0, out);
+}
+
+void launch_readback_total(const long long *total, Readback *out, cudaStream_t st)
+{
+    k_readback_total<<<1, 1, 0, st>>>(total, out);
+}
+
 __global__ void k_init_counters(Counters *ctr, int nroots)
 {
     Counters c = {};

@@ -30,6 +30,9 @@ void launch_level_finish(const TreeDev &T, const LevelBufs &L, const LevelHints 
 void launch_small(const TreeDev &T, const LevelBufs &L, long long nitems_hint, int sms, cudaStream_t st);
 int scan_tile_count(long long n);
 size_t small_smem_bytes();
+// Small read-backs into mapped pinned host memory (see Readback).
+void launch_readback(const Counters *ctr, const NodeWalk *walk0, Readback *out, cudaStream_t st);
+void launch_readback_total(const long long *total, Readback *out, cudaStream_t st);
 cudaError_t build_init_attributes();
 
 }  // namespace bt

@@ -941,12 +941,14 @@ constexpr int kScan64Tile = 2048;
 
 // Exclusive scan of int32 counts [n] into int64 offsets [n + 1] (three
 // passes: tile sums, one block over the tile sums, per-tile apply).
-__global__ void __launch_bounds__(256) k_scan64_tiles(const int32_t *in, long long n, long long *tsum)
+// cap: each count is taken as min(count, cap).
+__global__ void __launch_bounds__(256) k_scan64_tiles(const int32_t *in, long long n, int cap,
+                                                      long long *tsum)
 {
     __shared__ long long ws[8];
     const long long t0 = (long long)blockIdx.x * kScan64Tile;
     long long s = 0;
-    for (long long i = t0 + threadIdx.x; i < min(t0 + kScan64Tile, n); i += blockDim.x) s += in[i];
+    for (long long i = t0 + threadIdx.x; i < min(t0 + kScan64Tile, n); i += blockDim.x) s += min(in[i], cap);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(~0u, s, o);
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
     __syncthreads();
@@ -982,8 +984,8 @@ __global__ void __launch_bounds__(1024) k_scan64_sums(long long *tsum, int ntile
     if (threadIdx.x == 0) *total = carry;
 }
 
-__global__ void __launch_bounds__(256) k_scan64_apply(const int32_t *in, long long n, const long long *toff,
-                                                      long long *out)
+__global__ void __launch_bounds__(256) k_scan64_apply(const int32_t *in, long long n, int cap,
+                                                      const long long *toff, long long *out)
 {
     // 256 threads x 8 items
     __shared__ long long ws[8];
@@ -992,7 +994,7 @@ __global__ void __launch_bounds__(256) k_scan64_apply(const int32_t *in, long lo
     long long s = 0;
     for (int k = 0; k < 8; k++) {
         const long long i = t0 + threadIdx.x * 8 + k;
-        v[k] = i < n ? in[i] : 0;
+        v[k] = i < n ? min(in[i], cap) : 0;
         s += v[k];
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1017,6 +1019,9 @@ __global__ void k_copy_total(const long long *total, long long *dst) { *dst = *t
 
 long long csr_scratch_elems(long long n) { return (n + kScan64Tile - 1) / kScan64Tile + 2; }
 
+void launch_scan64(const int32_t *counts, long long n, int cap, long long *offsets, long long *scratch,
+                   cudaStream_t st);
+
 cudaError_t launch_find_csr_count(const TreeDev &T, int ngroups, int ngroups_c, int32_t *counts,
                                   const float *m, float *smass, float *rho, long long *offsets,
                                   long long *scratch, int sms, cudaStream_t st)
@@ -1037,17 +1042,52 @@ cudaError_t launch_find_csr_count(const TreeDev &T, int ngroups, int ngroups_c, 
     const long long n = T.n;
     const int ntiles = (int)((n + kScan64Tile - 1) / kScan64Tile);
     long long *total = scratch + ntiles;
+    launch_scan64(counts, n, INT_MAX, offsets, scratch, st);
+    return cudaGetLastError();
+}
+
+void launch_scan64(const int32_t *counts, long long n, int cap, long long *offsets, long long *scratch,
+                   cudaStream_t st)
+{
+    const int ntiles = (int)((n + kScan64Tile - 1) / kScan64Tile);
+    long long *total = scratch + ntiles;
     if (ntiles > 0) {
         note_launch(3);
-        k_scan64_tiles<<<ntiles, 256, 0, st>>>(counts, n, scratch);
+        k_scan64_tiles<<<ntiles, 256, 0, st>>>(counts, n, cap, scratch);
         k_scan64_sums<<<1, 1024, 0, st>>>(scratch, ntiles, total);
-        k_scan64_apply<<<ntiles, 256, 0, st>>>(counts, n, scratch, offsets);
+        k_scan64_apply<<<ntiles, 256, 0, st>>>(counts, n, cap, scratch, offsets);
     } else {
         cudaMemsetAsync(total, 0, sizeof(long long), st);
     }
     note_launch();
     k_copy_total<<<1, 1, 0, st>>>(total, offsets + n);
-    return cudaGetLastError();
+}
+
+// Pack fixed rows into compressed rows: row i's first min(counts[i], ngmax)
+// entries go to csr[offsets[i] ..].  One warp per row, coalesced.
+__global__ void __launch_bounds__(256) k_pack_rows(const int32_t *__restrict__ rows,
+                                                   const int32_t *__restrict__ counts, long long n,
+                                                   int ngmax, const long long *__restrict__ offsets,
+                                                   int32_t *__restrict__ csr)
+{
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
+        const int c = min(counts[i], ngmax);
+        const int32_t *src = rows + i * ngmax;
+        int32_t *dst = csr + offsets[i];
+        for (int k = lane; k < c; k += 32) dst[k] = src[k];
+    }
+}
+
+void launch_pack_rows(const int32_t *rows, const int32_t *counts, long long n, int ngmax,
+                      const long long *offsets, int32_t *csr, int sms, cudaStream_t st)
+{
+    long long blocks = (n + 7) / 8;
+    if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
+    if (blocks < 1) blocks = 1;
+    note_launch();
+    k_pack_rows<<<(int)blocks, 256, 0, st>>>(rows, counts, n, ngmax, offsets, csr);
 }
 
 cudaError_t launch_find_csr_rows(const TreeDev &T, int ngroups, int ngroups_c, const long long *offsets,

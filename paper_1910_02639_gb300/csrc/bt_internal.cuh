@@ -382,6 +382,16 @@ struct Src {
     }
 };
 
+// What the host reads back after a step.  The device writes it with an
+// ordinary store into mapped pinned host memory (no copy engine involved, so
+// small read-backs never queue behind a large copy on another stream).
+struct Readback {
+    Counters c;
+    long long total;  // a compressed-row total (btree_find_neighbors_csr / btree_pack_rows)
+    int root_b;       // branching factor of node 0
+    int pad;
+};
+
 // Buffers of the level-synchronous build of big cells.  Level L reads the
 // particles from the input (L = 0) or working buffer (L-1)&1 and writes
 // working buffer L&1; its big cells are ids[L&1], the next level's ids[(L+1)&1].

@@ -372,3 +372,33 @@ def test_k2_sets_trees_and_lists(bt, oracle):
     _, _, res3 = run_batched(bt, sets, None, ngmax=512)
     for i in range(len(sets)):
         _assert_same(res[i], res3[i], "set %d k=2 vs k=3" % i)
+
+
+def test_pack_rows_equals_csr_rows(bt):
+    import torch
+    sets = [wl.uniform_cube(20_000, seed=535, target=80), wl.sphere_1r(15_000, seed=536, target=120),
+            wl.uniform_cube(3_000, seed=537, target=60)]
+    g = 1024
+    tree, off, res = run_batched(bt, sets, ngmax=g)
+    dev = torch.device("cuda:0")
+    n = int(off[-1])
+    assert max(int(r["cnt"].max()) for r in res) <= g
+    # fixed rows again on the device, then packed
+    rows = torch.full((n * g,), -1, dtype=torch.int32, device=dev)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev)
+    bt.btree_find_neighbors(tree, g, rows, cnt)
+    offs_p = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    total = bt.btree_pack_rows(tree, rows, cnt, g, offs_p)
+    csr_p = torch.full((total,), -9, dtype=torch.int32, device=dev)
+    assert bt.btree_pack_rows(tree, rows, cnt, g, offs_p, csr_p) == total
+    offs_c = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    csr_c = torch.empty(total, dtype=torch.int32, device=dev)
+    assert bt.btree_find_neighbors_csr(tree, offs_c, csr_c) == total
+    assert torch.equal(offs_p, offs_c) and torch.equal(csr_p, csr_c)
+    # capped rows pack only their first ngmax entries
+    small = 8
+    rows8 = torch.empty(n * small, dtype=torch.int32, device=dev)
+    bt.btree_find_neighbors(tree, small, rows8, cnt)
+    t8 = bt.btree_pack_rows(tree, rows8, cnt, small, offs_p)
+    assert t8 == int(cnt.clamp(max=small).to(torch.int64).sum())
+    tree.free()
