@@ -203,6 +203,8 @@ int btree_find_neighbors(const btree_t *t, int ngmax, int32_t *neighbors,
  * btree_find_neighbors_csr -- FindNeighbors (Algorithm 2) into compressed
  * rows: every neighbour of every particle, no ngmax cap.  The paper has no
  * output format of its own; this is the compacted form of the same lists.
+ * flags     : 0, or BT_FIND_HALF: row i holds only {j in N(i) : j > i}
+ *             (symmetric half lists; no density with this flag).
  *
  * Two passes over the tree: the first counts (and, when m != NULL, computes
  * rho exactly as btree_find_neighbors_density does), an exclusive scan turns
@@ -219,7 +221,9 @@ int btree_find_neighbors(const btree_t *t, int ngmax, int32_t *neighbors,
  * total); the second pass is asynchronous.  Uses scratch owned by the tree
  * (counts and scan partials, allocated on first use).
  */
-int btree_find_neighbors_csr(const btree_t *t, const float *m, float *rho, int64_t *offsets,
+#define BT_FIND_HALF 1 /* rows hold only the neighbours j > i: with a uniform h the
+                          relation is symmetric and every pair appears once */
+int btree_find_neighbors_csr(const btree_t *t, int flags, const float *m, float *rho, int64_t *offsets,
                              int32_t *neighbors, int64_t capacity, int64_t *total, void *stream);
 
 /*

@@ -82,7 +82,7 @@ def _load():
                                                  ctypes.c_int, vp, vp, vp, vp, vp,
                                                  ctypes.POINTER(vp)]
         lib.btree_find_neighbors_csr.restype = ctypes.c_int
-        lib.btree_find_neighbors_csr.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int64,
+        lib.btree_find_neighbors_csr.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, ctypes.c_int64,
                                                  ctypes.POINTER(ctypes.c_int64), vp]
         lib.btree_pack_rows.restype = ctypes.c_int
         lib.btree_pack_rows.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp, ctypes.c_int64,
@@ -271,8 +271,11 @@ def btree_build_find_batched(x, y, z, h, offsets, ngmax: int, neighbors, counts,
     return t
 
 
+BT_FIND_HALF = 1
+
+
 def btree_find_neighbors_csr(tree: Tree, offsets, neighbors=None, m=None, rho=None,
-                             stream=None) -> int:
+                             stream=None, half: bool = False) -> int:
     """Compressed rows: offsets (int64 [n+1]) always written; rows written
     into `neighbors` (int32, any size >= the total) when given.  Returns the
     total number of pairs.  With neighbors=None only the offsets (and the
@@ -288,7 +291,8 @@ def btree_find_neighbors_csr(tree: Tree, offsets, neighbors=None, m=None, rho=No
     pn = _dptr(neighbors, torch.int32, "neighbors") if neighbors is not None else None
     cap = int(neighbors.numel()) if neighbors is not None else 0
     tot = ctypes.c_int64(0)
-    st = lib.btree_find_neighbors_csr(tree.handle, pm, pr, po, pn, cap, ctypes.byref(tot),
+    st = lib.btree_find_neighbors_csr(tree.handle, BT_FIND_HALF if half else 0, pm, pr, po, pn, cap,
+                                      ctypes.byref(tot),
                                       ctypes.c_void_p(_stream_ptr(stream)))
     _check(st, "btree_find_neighbors_csr")
     return int(tot.value)

@@ -811,11 +811,13 @@ int btree_pack_rows(const btree_t *tc, const int32_t *rows, const int32_t *count
     return to_status(cudaGetLastError());
 }
 
-int btree_find_neighbors_csr(const btree_t *tc, const float *m, float *rho, int64_t *offsets,
+int btree_find_neighbors_csr(const btree_t *tc, int flags, const float *m, float *rho, int64_t *offsets,
                              int32_t *neighbors, int64_t capacity, int64_t *total, void *stream)
 {
     btree *t = const_cast<btree *>(tc);
     if (!t || !offsets || (m == nullptr) != (rho == nullptr) || capacity < 0) return BT_ERR_ARG;
+    if ((flags & ~BT_FIND_HALF) || ((flags & BT_FIND_HALF) && m)) return BT_ERR_ARG;
+    const int half = (flags & BT_FIND_HALF) ? 1 : 0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t n = t->n;
     if (n == 0) {
@@ -841,7 +843,8 @@ int btree_find_neighbors_csr(const btree_t *tc, const float *m, float *rho, int6
     if (!ok) return BT_ERR_OOM;
     const TreeDev T = view(t);
     cudaError_t e = launch_find_csr_count(T, t->ngroups, t->ngroups_c, t->csr_counts, m, t->smass, rho,
-                                          reinterpret_cast<long long *>(offsets), t->csr_scratch, t->sms, st);
+                                          reinterpret_cast<long long *>(offsets), t->csr_scratch, half,
+                                          t->sms, st);
     if (e != cudaSuccess) return to_status(e);
     launch_readback_total(reinterpret_cast<const long long *>(offsets + n), t->rb_dev, st);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return to_status(e);
@@ -851,7 +854,7 @@ int btree_find_neighbors_csr(const btree_t *tc, const float *m, float *rho, int6
     if (tot > capacity) return BT_ERR_CAPACITY;
     return to_status(launch_find_csr_rows(T, t->ngroups, t->ngroups_c,
                                           reinterpret_cast<const long long *>(offsets), neighbors,
-                                          t->csr_counts, t->sms, st));
+                                          t->csr_counts, half, t->sms, st));
 }
 
 int sph_density(const btree_t *t, const float *m, const int32_t *neighbors, const int32_t *counts,

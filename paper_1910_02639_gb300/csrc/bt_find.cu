@@ -73,6 +73,7 @@ struct FindSmem {
     float qh[kGroupMax];
     int qorig[kGroupMax];
     int qself[kGroupMax];     // sorted position of the query itself, or -1
+    int qlow[kGroupMax];      // half rows: candidates below this sorted position are dropped
     int qcnt[kGroupMax];
     int front[2][kFrontMax];  // walk frontiers
     int fr_rx0[kFrontMax], fr_rx1[kFrontMax], fr_ry0[kFrontMax], fr_ny[kFrontMax];
@@ -98,6 +99,7 @@ struct FindArgs {
     // (null: fixed rows of ngmax); count_only: counts (and density), no rows
     const long long *row_off;
     int count_only;
+    int half;  // rows hold only j > i (each pair once when h is uniform)
 };
 
 __device__ __forceinline__ float warp_min(float v)
@@ -489,6 +491,8 @@ __device__ void group_window(const FindArgs &A, FindSmem<C> &S, bool presorted)
             if ((S.key[mid] >> C::SLOT_BITS) < want) lo = mid + 1; else hi = mid;
         }
         S.qself[tid] = (o >= kmin && lo < m && (S.key[lo] >> C::SLOT_BITS) == want) ? lo : -1;
+        // half rows keep j > i only: drop every candidate up to the query itself
+        S.qlow[tid] = o < kmin ? 0 : (S.qself[tid] >= 0 ? lo + 1 : lo);
     }
 
     // ---- stage A: one ballot per (query, chunk); two chunks per pass
@@ -538,6 +542,12 @@ __device__ void group_window(const FindArgs &A, FindSmem<C> &S, bool presorted)
         uint32_t mk = lane < nch ? S.mask[p * C::CHUNKS + lane] : 0u;
         const int sr = S.qself[p];
         if (sr >= 0 && lane == (sr >> 5)) mk &= ~(1u << (sr & 31));
+        if (A.half) {
+            const int low = S.qlow[p];
+            const int c0 = lane * 32;
+            if (c0 + 32 <= low) mk = 0u;
+            else if (c0 < low) mk &= ~((1u << (low - c0)) - 1u);
+        }
         const int cnt = __popc(mk);
         int incl = cnt;
         for (int o = 1; o < 32; o <<= 1) {
@@ -914,6 +924,7 @@ cudaError_t launch_find(const TreeDev &T, int ngroups, int ngroups_c, int ngmax,
     A.list = 0;
     A.row_off = nullptr;
     A.count_only = 0;
+    A.half = 0;
     return launch_find_rows(A, T, ngroups, ngroups_c, m, sms, st);
 }
 
@@ -1024,9 +1035,10 @@ void launch_scan64(const int32_t *counts, long long n, int cap, long long *offse
 
 cudaError_t launch_find_csr_count(const TreeDev &T, int ngroups, int ngroups_c, int32_t *counts,
                                   const float *m, float *smass, float *rho, long long *offsets,
-                                  long long *scratch, int sms, cudaStream_t st)
+                                  long long *scratch, int half, int sms, cudaStream_t st)
 {
     FindArgs A;
+    A.half = half;
     A.T = T;
     A.ngmax = 0;
     A.nbrs = nullptr;
@@ -1091,9 +1103,10 @@ void launch_pack_rows(const int32_t *rows, const int32_t *counts, long long n, i
 }
 
 cudaError_t launch_find_csr_rows(const TreeDev &T, int ngroups, int ngroups_c, const long long *offsets,
-                                 int32_t *nbrs, int32_t *counts, int sms, cudaStream_t st)
+                                 int32_t *nbrs, int32_t *counts, int half, int sms, cudaStream_t st)
 {
     FindArgs A;
+    A.half = half;
     A.T = T;
     A.ngmax = 0;
     A.nbrs = nbrs;

@@ -19,7 +19,7 @@ long long noalloc_max_particles();
 long long csr_scratch_elems(long long n);
 cudaError_t launch_find_csr_count(const TreeDev &T, int ngroups, int ngroups_c, int32_t *counts,
                                   const float *m, float *smass, float *rho, long long *offsets,
-                                  long long *scratch, int sms, cudaStream_t st);
+                                  long long *scratch, int half, int sms, cudaStream_t st);
 // Exclusive scan of min(counts, cap) into offsets [n + 1]; pack fixed rows
 // into compressed rows.
 void launch_scan64(const int32_t *counts, long long n, int cap, long long *offsets, long long *scratch,
@@ -27,7 +27,7 @@ void launch_scan64(const int32_t *counts, long long n, int cap, long long *offse
 void launch_pack_rows(const int32_t *rows, const int32_t *counts, long long n, int ngmax,
                       const long long *offsets, int32_t *csr, int sms, cudaStream_t st);
 cudaError_t launch_find_csr_rows(const TreeDev &T, int ngroups, int ngroups_c, const long long *offsets,
-                                 int32_t *nbrs, int32_t *counts, int sms, cudaStream_t st);
+                                 int32_t *nbrs, int32_t *counts, int half, int sms, cudaStream_t st);
 size_t find_smem_bytes();
 cudaError_t find_init_attributes();
 

@@ -402,3 +402,36 @@ def test_pack_rows_equals_csr_rows(bt):
     t8 = bt.btree_pack_rows(tree, rows8, cnt, small, offs_p)
     assert t8 == int(cnt.clamp(max=small).to(torch.int64).sum())
     tree.free()
+
+
+def test_half_rows_are_the_upper_half_of_the_full_rows(bt):
+    import torch
+    # uniform h: the relation is symmetric, every pair once; variable h: still
+    # exactly {j in N(i) : j > i}
+    sets = [wl.jittered_slab(30, 20, 12, jitter=0.1, h=1.5, seed=538), wl.evrard(8_000, seed=539, target=60),
+            wl.plummer(3_000, seed=540, target=80)]
+    dev = torch.device("cuda:0")
+    off, *arrs = _concat(sets)
+    x, y, z, h, m = (torch.from_numpy(a).to(dev) for a in arrs)
+    n = int(off[-1])
+    tree = bt.btree_build_batched(x, y, z, h, off, [dict(), dict(find_compact=True), dict(bucket_size=8)])
+    of = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    tot = bt.btree_find_neighbors_csr(tree, of)
+    full = torch.empty(tot, dtype=torch.int32, device=dev)
+    bt.btree_find_neighbors_csr(tree, of, full)
+    oh = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    toth = bt.btree_find_neighbors_csr(tree, oh, half=True)
+    halfr = torch.empty(toth, dtype=torch.int32, device=dev)
+    bt.btree_find_neighbors_csr(tree, oh, halfr, half=True)
+    with pytest.raises(bt.BtreeError):
+        bt.btree_find_neighbors_csr(tree, oh, m=m, rho=torch.empty_like(m), half=True)
+    torch.cuda.synchronize()
+    of, full, oh, halfr = of.cpu().numpy(), full.cpu().numpy(), oh.cpu().numpy(), halfr.cpu().numpy()
+    for i in range(n):
+        s_ = np.searchsorted(off, i, side="right") - 1
+        local = i - off[s_]
+        row = full[of[i]:of[i + 1]]
+        assert np.array_equal(halfr[oh[i]:oh[i + 1]], row[row > local]), "row %d" % i
+    a, b = int(off[0]), int(off[1])
+    assert 2 * (oh[b] - oh[a]) == of[b] - of[a]  # the slab (uniform h): each pair once
+    tree.free()
