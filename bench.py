@@ -222,6 +222,7 @@ def run_gpu(args):
                work_unit=params.get("group_size") or 32,
                find_shape="4 warps, 512-candidate window" if params.get("find_compact")
                else "8 warps, 1024-candidate window",
+               pack_leaves=bool(params.get("pack_leaves")),
                tuned=not args.no_tune and not args.params)
     offs = [0, n]
 
@@ -498,7 +499,8 @@ def run_batched_section(args, bt, dev, stream, dist, rank, ws):
                                                 for v in (plain_ms, batched_ms, tuned_ms, graph_ms))
     ds.free()
     rate = lambda ms: all_pairs / (ms * 1e-3)
-    table = {str(k): {kk: v[kk] for kk in ("bucket_size", "beta", "group_size", "find_compact")}
+    table = {"%d,%d" % k: {kk: v.get(kk) for kk in ("bucket_size", "beta", "group_size", "find_compact",
+                                                    "pack_leaves")}
              for k, v in tuner.table.items()}
     return {"workload": f"batched_{args.batched_sets}_sets", "n": int(sum(sp[1] for sp in specs)),
             "nsets": len(specs), "ngmax": ngmax, "scaling": "strong", "sets_per_rank": len(mine),

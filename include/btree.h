@@ -125,9 +125,13 @@ int btree_build(const float *x, const float *y, const float *z, const float *h,
                                  and y only (b^2 sub-cells), z never split.  The
                                  neighbour lists are those of the 3-D distance, so
                                  a planar set (z = 0) gets the 2-D lists. */
+#define BT_SET_PACK_LEAVES 8  /* sibling leaves adjacent in tree order share find
+                                 work units (up to group_size particles): fewer,
+                                 fuller units; same results */
 typedef struct {
     int bucket_size; /* s >= 1                                  */
-    int flags;       /* 0 or BT_SET_OCTREE | BT_SET_FIND_COMPACT | BT_SET_2D */
+    int flags;       /* 0 or BT_SET_OCTREE | BT_SET_FIND_COMPACT | BT_SET_2D |
+                        BT_SET_PACK_LEAVES */
     double alpha;    /* underfull fraction (Eq. 4), e.g. 0.5    */
     double beta;     /* empty-cell limit (Eq. 4), e.g. 0.5      */
     int group_size;  /* queries searched together (a find work

@@ -189,6 +189,7 @@ def btree_build(x, y, z, h, bucket_size: int = 16, alpha: float = 0.5, beta: flo
 BT_SET_OCTREE = 1
 BT_SET_FIND_COMPACT = 2
 BT_SET_2D = 4
+BT_SET_PACK_LEAVES = 8
 
 
 class _SetParams(ctypes.Structure):
@@ -208,7 +209,8 @@ def _set_params(params, nsets):
         c_par[i].bucket_size = int(p.get("bucket_size", 16))
         c_par[i].flags = ((BT_SET_OCTREE if p.get("octree", False) else 0) |
                           (BT_SET_FIND_COMPACT if p.get("find_compact", False) else 0) |
-                          (BT_SET_2D if int(p.get("dim", 3)) == 2 else 0))
+                          (BT_SET_2D if int(p.get("dim", 3)) == 2 else 0) |
+                          (BT_SET_PACK_LEAVES if p.get("pack_leaves", False) else 0))
         c_par[i].alpha = float(p.get("alpha", 0.5))
         c_par[i].beta = float(p.get("beta", 0.5))
         c_par[i].group_size = int(p.get("group_size", 0))

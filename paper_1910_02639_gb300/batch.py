@@ -22,7 +22,7 @@ from . import (btree_build, btree_build_batched, btree_build_find_batched,
                btree_find_neighbors_density)
 
 DEFAULT_PARAMS = dict(bucket_size=16, alpha=0.5, beta=0.5, octree=False, group_size=0,
-                      find_compact=False, dim=3)
+                      find_compact=False, dim=3, pack_leaves=False)
 
 
 def offsets_of(sizes) -> np.ndarray:
@@ -88,7 +88,8 @@ class DeviceSets:
             if b == a:
                 continue
             p = pl[i]
-            if p.get("octree") or p.get("group_size") or p.get("find_compact") or p.get("dim", 3) != 3:
+            if (p.get("octree") or p.get("group_size") or p.get("find_compact") or p.get("pack_leaves")
+                    or p.get("dim", 3) != 3):
                 raise ValueError("the plain path takes bucket_size, alpha and beta only")
             t = btree_build(self.x[a:b], self.y[a:b], self.z[a:b], self.h[a:b],
                             bucket_size=p["bucket_size"], alpha=p["alpha"], beta=p["beta"],

@@ -679,7 +679,8 @@ static int stage_batched(const float *x, const float *y, const float *z, const f
         const int s = params ? params[i].bucket_size : 16;
         const double a = params ? params[i].alpha : 0.5, b = params ? params[i].beta : 0.5;
         if (s < 1 || s > (1 << 20) || !is_finite_d(a) || !is_finite_d(b)) return BT_ERR_ARG;
-        if (params && (params[i].flags & ~(BT_SET_OCTREE | BT_SET_FIND_COMPACT | BT_SET_2D))) return BT_ERR_ARG;
+        if (params && (params[i].flags & ~(BT_SET_OCTREE | BT_SET_FIND_COMPACT | BT_SET_2D | BT_SET_PACK_LEAVES)))
+            return BT_ERR_ARG;
         if (params && (params[i].group_size < 0 || params[i].group_size > kGroupMax)) return BT_ERR_ARG;
         smin = std::min(smin, s);
     }
@@ -697,7 +698,8 @@ static int stage_batched(const float *x, const float *y, const float *z, const f
         const double a = params ? params[i].alpha : 0.5, b = params ? params[i].beta : 0.5;
         const int f = (params && (params[i].flags & BT_SET_OCTREE) ? kSetOctree : 0) |
                       (params && (params[i].flags & BT_SET_FIND_COMPACT) ? kSetFindCompact : 0) |
-                      (params && (params[i].flags & BT_SET_2D) ? kSetTwoD : 0);
+                      (params && (params[i].flags & BT_SET_2D) ? kSetTwoD : 0) |
+                      (params && (params[i].flags & BT_SET_PACK_LEAVES) ? kSetPackLeaves : 0);
         const int g = params && params[i].group_size > 0 ? params[i].group_size : kGroupMax;
         stage_set(t, i, offsets[i], offsets[i + 1], s, a, b, f, g);
     }

@@ -621,7 +621,22 @@ __global__ void __launch_bounds__(256) k_big_emit(TreeDev T, LevelBufs L)
                 atomicAdd(&T.ctr->noversized, 1);
                 atomicOr(&T.ctr->status, kStOversized);
             }
-            emit_groups(T, c.set, start, cnt);
+            if (!(T.set_flags[c.set] & kSetPackLeaves)) {
+                emit_groups(T, c.set, start, cnt);
+            } else {
+                // leaf sub-cells 2i and 2i+1 (adjacent in tree order) share
+                // a work unit when both are leaves and fit together
+                const int nc = ncells(b, kd), gm = T.set_gmax[c.set];
+                const int jp = j ^ 1;  // the partner sub-cell
+                bool paired = false;
+                if (jp < nc) {
+                    const int cp = hist[c.hist_base + jp];
+                    const bool leafp = cp > 0 && !(cp > s && depth < kDepthMax);
+                    paired = leafp && cnt + cp <= gm;
+                }
+                if (!paired) emit_groups(T, c.set, start, cnt);
+                else if ((j & 1) == 0) emit_groups(T, c.set, start, cnt + hist[c.hist_base + jp]);
+            }
         }
         T.slots[c.slot0 + j] = Slot{start, cnt, child, 0};
     }
@@ -818,6 +833,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
         const int s_set = T.set_s[set];
         const int na = T.set_na[set];
         const bool octree = (T.set_flags[set] & kSetOctree) != 0;
+        const bool pack = (T.set_flags[set] & kSetPackLeaves) != 0;
         const int kd = set_dim(T, set);
         const Src &src = item.src == 0 ? src0 : (item.src == 1 ? src1 : srcin);
         for (int k = lane; k < m0; k += 32) {
@@ -979,10 +995,39 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                             atomicAdd(&T.ctr->noversized, 1);
                             atomicOr(&T.ctr->status, kStOversized);
                         }
-                        if (F.emit) emit_groups(T, set, start, cnt);
+                        if (F.emit && !pack) emit_groups(T, set, start, cnt);
                     }
                     T.slots[slot0 + j] = Slot{start, cnt, child, 0};
                 }
+                if (F.emit && pack && lane == 0) {
+                    // sibling leaves in sub-cell order are adjacent in tree
+                    // order: pack runs of them along one x-row of sub-cells
+                    // (so that a unit stays compact) into units of <= gmax
+                    const int gm = T.set_gmax[set];
+                    const int depth = F.depth + 1;
+                    int ps = 0, pc = 0, prow = -1;
+                    for (int j = 0; j < ncell; j++) {
+                        const int cnt = S.hist[j];
+                        if (cnt == 0) continue;
+                        const int start = base + a + S.off[j];
+                        if (cnt > s_set && depth < kDepthMax) {  // an internal sub-cell
+                            if (pc > 0) emit_groups(T, set, ps, pc);
+                            pc = 0;
+                            continue;
+                        }
+                        const int row = j / b;
+                        if (pc > 0 && pc + cnt <= gm && start == ps + pc && row == prow) {
+                            pc += cnt;
+                        } else {
+                            if (pc > 0) emit_groups(T, set, ps, pc);
+                            ps = start;
+                            pc = cnt;
+                            prow = row;
+                        }
+                    }
+                    if (pc > 0) emit_groups(T, set, ps, pc);
+                }
+                __syncwarp();  // S.hist / S.off are rewritten by the scatter below
                 if (lane == 0) {
                     NodeWalk w;
                     make_walk(g, b, slot0, w, kd);

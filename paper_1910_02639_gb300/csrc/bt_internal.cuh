@@ -305,6 +305,7 @@ enum : int {
     kSetLeafRoot = 2,  // the whole set fits one leaf
     kSetFindCompact = 4,  // searched by the compact block shape (4 warps, 512 candidates)
     kSetTwoD = 8,         // k = 2: cells split in x and y only (b^2 sub-cells)
+    kSetPackLeaves = 16,  // sibling leaves adjacent in tree order share work units
 };
 
 // Work units are (first tree position, set << 6 | count), count <= 32.

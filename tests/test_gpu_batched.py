@@ -161,6 +161,8 @@ def test_batched_argument_errors(bt):
     dict(group_size=8), dict(group_size=16), dict(group_size=1),
     dict(bucket_size=64, beta=0.25, group_size=16), dict(bucket_size=8, beta=0.75),
     dict(find_compact=True), dict(find_compact=True, bucket_size=8, group_size=16),
+    dict(pack_leaves=True), dict(pack_leaves=True, bucket_size=8, beta=0.25, find_compact=True),
+    dict(pack_leaves=True, bucket_size=4, group_size=16),
     [dict(find_compact=bool(i % 2), bucket_size=(8, 16, 32)[i % 3]) for i in range(10)],
 ])
 def test_tuning_knobs_never_change_results(bt, params):
@@ -196,11 +198,11 @@ def test_plain_path_helper_matches_batched(bt):
 
 
 def test_autotuner_table_and_params(bt):
-    from paper_1910_02639_gb300.autotune import Tuner, size_class
+    from paper_1910_02639_gb300.autotune import Tuner, set_class
     sets = wl.batched_sets(6, seed=517, nmin=2_000, nmax=50_000)
     tu = Tuner("cuda:0", NGMAX, reps=1, sample_particles=100_000)
     table = tu.tune(sets)
-    assert set(table) == {size_class(s.n) for s in sets}
+    assert set(table) == {set_class(s) for s in sets}
     for e in table.values():
         assert e["bucket_size"] in (8, 16, 32, 64) and e["beta"] in (0.25, 0.5, 0.75)
         assert e["group_size"] in (16, 32) and e["find_compact"] in (False, True) and e["ms"] > 0

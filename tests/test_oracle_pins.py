@@ -435,3 +435,4 @@ def test_k2_tree_never_splits_z_and_lists_are_the_definition(oracle):
     # the 8 points at distance 1 and sqrt(2)
     interior = (x >= 2) & (x <= 27) & (y >= 2) & (y <= 17)
     assert np.all(cnt2[interior] == 8)
+
