@@ -52,7 +52,7 @@ constexpr int kFrontMax = 64;              // tree nodes per walk frontier
 constexpr int kDescendMin = 32;            // smaller internal sub-cells are scanned whole
 constexpr int kFindChunk = 4;              // consecutive groups per block step
 constexpr int kHitBatch = 256;             // hit positions staged per warp and pass
-constexpr int kUnroll = 4;                 // gather jobs in flight per warp
+constexpr int kUnroll = 2;                 // gather jobs in flight per warp (more spills registers)
 constexpr int kSortThreads = 128;          // warps 0-3 sort; the others wait
 constexpr float kPiF = 3.14159265358979f;
 
@@ -1051,10 +1051,7 @@ cudaError_t launch_find_csr_count(const TreeDev &T, int ngroups, int ngroups_c, 
     A.count_only = 1;
     cudaError_t e = launch_find_rows(A, T, ngroups, ngroups_c, m, sms, st);
     if (e != cudaSuccess) return e;
-    const long long n = T.n;
-    const int ntiles = (int)((n + kScan64Tile - 1) / kScan64Tile);
-    long long *total = scratch + ntiles;
-    launch_scan64(counts, n, INT_MAX, offsets, scratch, st);
+    launch_scan64(counts, T.n, INT_MAX, offsets, scratch, st);
     return cudaGetLastError();
 }
 
