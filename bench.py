@@ -81,9 +81,9 @@ def find_kernel_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes per launch of the find kernel from the committed ncu summary,
-    if it was taken on the current kernel source."""
+def _profile_kv(workload: str):
+    """Machine-readable lines of the committed ncu summary of the find
+    kernel, if it was taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", f"k_find_{workload}.md")
     if not os.path.exists(p):
         return None
@@ -92,12 +92,30 @@ def profiled_traffic(workload: str):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("source_sha") != find_kernel_sha():
-        return None
+    return kv if kv.get("source_sha") == find_kernel_sha() else None
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the find kernel (ncu, scaled to the workload)."""
+    kv = _profile_kv(workload)
     try:
-        return float(kv["dram_bytes_per_launch_scaled"])
+        return float(kv["dram_bytes_per_launch_scaled"]) if kv else None
     except (KeyError, ValueError):
         return None
+
+
+def profiled_warp_insts(workload: str):
+    """Warp instructions per launch of the find kernel (ncu, scaled)."""
+    kv = _profile_kv(workload)
+    try:
+        return float(kv["warp_insts_per_launch_scaled"]) if kv else None
+    except (KeyError, ValueError):
+        return None
+
+
+def issue_peak(sm_mhz):
+    """Peak warp-instruction issue rate: 152 SMs x 4 schedulers x 1 per clock."""
+    return 152 * 4 * (sm_mhz or 2070.0) * 1e6
 
 
 # ---------------------------------------------------------------- clocks
@@ -317,6 +335,7 @@ def run_gpu(args):
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": alg_bytes, "peak_kind": peak_kind}
+    insts = profiled_warp_insts(cfg["workload"])
     step_ach = alg_bytes / (step_ms * 1e-3) / 1e9
     step_roofline = {"achieved": round(step_ach, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(step_ach / peak, 4), "note": "same algorithmic bytes over build+find"}
@@ -341,6 +360,17 @@ def run_gpu(args):
                           "form": "btree_build_find_batched: build+find+density as one CUDA graph "
                                   "launch per step (device-side level and ratio loops)"},
            "clocks": sampler.summary(t0, t1g)}
+    if insts:
+        # the kernel is instruction-bound: its issue rate against the SMs' peak
+        rate = insts / (find_ms * 1e-3)
+        pk = issue_peak(out["clocks"].get("sm_mhz"))
+        out["issue_roofline"] = {"bound": "issue", "kernel": roofline["kernel"],
+                                 "achieved": round(rate / 1e12, 4), "peak": round(pk / 1e12, 4),
+                                 "unit": "Twarp-inst/s", "frac": round(rate / pk, 4),
+                                 "warp_insts_per_launch": insts,
+                                 "note": "instructions from the committed ncu capture (scaled to the "
+                                         "workload) over the event-timed launch; peak = 152 SMs x 4 "
+                                         "schedulers x SM clock"}
 
     # ---- many uneven sets: batched vs the plain per-set path
     if not args.no_batched:
