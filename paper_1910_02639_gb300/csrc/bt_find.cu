@@ -497,6 +497,7 @@ __device__ void group_window(const FindArgs &A, FindSmem<C> &S, bool presorted)
 
     // ---- stage A: one ballot per (query, chunk); two chunks per pass
     const int nch = (m + 31) >> 5;
+    const bool halves = nch <= 16;  // stage B: two lanes per chunk
     for (int c = warp; c < nch; c += 2 * C::WARPS) {
         const int c2 = c + C::WARPS;
         const bool has2 = c2 < nch;
@@ -539,15 +540,22 @@ __device__ void group_window(const FindArgs &A, FindSmem<C> &S, bool presorted)
     // write the row (and the density terms) lane-parallel in ascending order.
     unsigned short *hl = S.hits[warp];
     for (int p = warp; p < gcount; p += C::WARPS) {
-        uint32_t mk = lane < nch ? S.mask[p * C::CHUNKS + lane] : 0u;
+        // lane -> (chunk, half): with at most 16 chunks every chunk's mask
+        // is split over two lanes (16 candidates each), so the extraction
+        // loop below runs half as long; lanes stay in candidate order
+        const int ch = halves ? (lane >> 1) : lane;
+        uint32_t mk = ch < nch ? S.mask[p * C::CHUNKS + ch] : 0u;
         const int sr = S.qself[p];
-        if (sr >= 0 && lane == (sr >> 5)) mk &= ~(1u << (sr & 31));
+        if (sr >= 0 && ch == (sr >> 5)) mk &= ~(1u << (sr & 31));
         if (A.half) {
             const int low = S.qlow[p];
-            const int c0 = lane * 32;
+            const int c0 = ch * 32;
             if (c0 + 32 <= low) mk = 0u;
             else if (c0 < low) mk &= ~((1u << (low - c0)) - 1u);
         }
+        const int sh16 = halves ? (lane & 1) * 16 : 0;
+        if (halves) mk = (mk >> sh16) & 0xffffu;
+        const int bitbase = ch * 32 + sh16;  // candidate of bit 0 of mk
         const int cnt = __popc(mk);
         int incl = cnt;
         for (int o = 1; o < 32; o <<= 1) {
@@ -572,7 +580,7 @@ __device__ void group_window(const FindArgs &A, FindSmem<C> &S, bool presorted)
                 uint32_t mm = mk;
                 int r = excl;
                 while (mm) {
-                    hl[r++] = (unsigned short)(lane * 32 + __ffs(mm) - 1);
+                    hl[r++] = (unsigned short)(bitbase + __ffs(mm) - 1);
                     mm &= mm - 1;
                 }
             } else if (excl < b0 + kHitBatch && excl + cnt > b0) {
@@ -581,7 +589,7 @@ __device__ void group_window(const FindArgs &A, FindSmem<C> &S, bool presorted)
                 while (mm) {
                     const int bit = __ffs(mm) - 1;
                     mm &= mm - 1;
-                    if (r >= b0 && r < b0 + kHitBatch) hl[r - b0] = (unsigned short)(lane * 32 + bit);
+                    if (r >= b0 && r < b0 + kHitBatch) hl[r - b0] = (unsigned short)(bitbase + bit);
                     r++;
                 }
             }
