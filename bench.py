@@ -577,6 +577,8 @@ def run_serving_section(args, dev, dist, rank, ws):
 
     def grab(tag):
         def f(res):
+            if res.error is not None:
+                raise RuntimeError(f"request {res.rid} failed: {res.error}")
             c = int(res.cnt.to(torch.int64).sum().item())
             rb = int(res.rho.view(torch.int32).to(torch.int64).sum().item())
             sums[(tag, res.rid)] = (c, list_checksum(res.nb, res.cnt, ngmax), rb)

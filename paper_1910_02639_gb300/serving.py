@@ -12,9 +12,12 @@ on the device.
 
 Results stay in device memory (views of the batch's output buffers) until the
 client releases them; the batch's memory returns to the budget when all of
-its results are released.  Each request's lists, counts and densities are
-bit-identical to those of the same set run alone: sets in a batch do not
-interact, and every per-particle result depends only on its own set.
+its results are released.  A request the library rejects (non-finite
+coordinates or smoothing lengths) fails alone: its batch is re-run request by
+request and only it returns an error result.  Each request's lists, counts
+and densities are bit-identical to those of the same set run alone: sets in a
+batch do not interact, and every per-particle result depends only on its own
+set.
 """
 from __future__ import annotations
 
@@ -26,7 +29,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import btree_build, btree_build_batched, btree_find_neighbors_density
+from . import BtreeError, btree_build, btree_build_batched, btree_find_neighbors_density
 
 
 def request_bytes(n: int, ngmax: int) -> int:
@@ -65,6 +68,7 @@ class Result:
     batch: int
     batch_size: int
     _batch_ref: object = None
+    error: str | None = None       # set when the request failed (then nb/cnt/rho are None)
 
     @property
     def latency(self) -> float:
@@ -153,7 +157,8 @@ class Server:
             return None
 
     def release(self, res: Result):
-        """Give a result's device memory back (after the client is done)."""
+        """Give a result's device memory back (after the client is done);
+        failed requests hold none."""
         b = res._batch_ref
         res._batch_ref = None
         res.nb = res.cnt = res.rho = None
@@ -211,6 +216,22 @@ class Server:
             bid, reqs, nbytes, t_adm = job
             try:
                 self._run_batch(slot, st, bid, reqs, nbytes, t_adm)
+            except BtreeError:
+                # a request of the batch failed (e.g. non-finite input): run
+                # each request alone, within the memory the batch holds, so
+                # that only the bad ones fail
+                held = nbytes
+                for r in reqs:
+                    one = request_bytes(r.n, self.ngmax)
+                    try:
+                        self._run_batch(slot, st, bid, [r], one, t_adm)
+                        held -= one  # now owned by that result's buffers
+                    except BtreeError as e1:
+                        self._done.put(Result(r.rid, r.n, None, None, None, r.arrival, t_adm,
+                                              self.now(), bid, 1, None, error=str(e1)))
+                    except BaseException as e1:  # not a request error: report it
+                        self.errors.append(e1)
+                self._return_bytes(held)
             except BaseException as e:  # reported to the caller, slot stays usable
                 self.errors.append(e)
                 self._return_bytes(nbytes)

@@ -81,3 +81,29 @@ def test_oversized_request_is_refused(srv_mod):
             srv.submit(r)
     finally:
         srv.close()
+
+
+def test_a_bad_request_fails_alone(srv_mod):
+    reqs = _requests(srv_mod, 6, seed=704, nmin=2_000, nmax=20_000)
+    reqs[3].x[5] = float("nan")  # pinned host copy: poisoned input
+    served, alone = {}, {}
+    errors = {}
+
+    def grab(res):
+        if res.error is not None:
+            errors[res.rid] = res.error
+        else:
+            _grab(served)(res)
+    srv = srv_mod.Server(ngmax=NGMAX, slots=1, max_batch_particles=200_000)
+    try:
+        out = srv_mod.replay(srv, reqs, on_result=grab)
+    finally:
+        srv.close()
+    assert len(out) == len(reqs) and not srv.errors
+    assert set(errors) == {3} and "non-finite" in errors[3]
+    good = [r for r in reqs if r.rid != 3]
+    srv_mod.replay_plain(good, ngmax=NGMAX, on_result=_grab(alone))
+    for r in good:
+        a, b = served[r.rid], alone[r.rid]
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        assert np.array_equal(a[2].view(np.int32), b[2].view(np.int32))
