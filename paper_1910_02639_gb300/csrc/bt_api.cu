@@ -1,5 +1,7 @@
-// bt_api.cu -- the C ABI (include/btree.h): tree handle, buffers, and the
-// host side of BuildTree (level loop over cells with > kSmallCap particles).
+// bt_api.cu -- the C ABI (include/btree.h): tree handle, buffers, the host
+// side of BuildTree (the level loop over cells with > kSmallCap particles,
+// host-driven or captured as a CUDA graph with device-driven loops), and the
+// search, compressed-row and read-back entry points.
 #include "bt_build.cuh"
 #include "bt_find.cuh"
 #include "bt_internal.cuh"

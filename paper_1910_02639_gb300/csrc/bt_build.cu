@@ -13,7 +13,13 @@
 // float h, in "tree order" once final: the particles of every cell, and so of
 // every sub-tree, occupy one contiguous range, sub-cells in id order.  Each
 // set's particles stay inside that set's input range; node i < nsets is the
-// root of set i.
+// root of set i.  Per set: k = 3 or 2 (b^k sub-cells, z not split), or the
+// octree (b = 2).
+//
+// Every level kernel reads its work counts from the device counters and
+// stops when the abort flag is set, so the level loop and the ratio loop can
+// be driven by the host (reading the counters) or by conditional nodes of a
+// CUDA graph (the one-thread kernels set the loop conditions).
 #include "bt_internal.cuh"
 #include "bt_build.cuh"
 

@@ -2,9 +2,10 @@
 // optionally fused with the SPH density sum (M4 cubic spline).
 //
 // Work unit: a group of <= 32 particles contiguous in tree order (a leaf, a
-// cell of <= 32 particles, or a slice of an oversized leaf), one 256-thread
-// block at a time (blocks are persistent and stride over the groups).  Per
-// group:
+// cell of <= 32 particles, a run of sibling leaves, or a slice of an
+// oversized leaf) of one particle set, one block at a time (blocks are
+// persistent and stride over the groups).  Two block shapes, chosen per set:
+// 8 warps with a 1024-candidate window, or 4 warps with 512.  Per group:
 //   1. warp 0 loads the queries; then all threads walk the tree once for the
 //      union of their search intervals (Eqs. 5-6 applied to the group's query
 //      box), frontier by frontier, collecting contiguous particle ranges
@@ -14,6 +15,7 @@
 //      flight per lane and keep the candidates within 2*h_max of the group's
 //      bounding box;
 //   3. the kept candidates are sorted by original index (bitonic, registers);
+//      in scan mode (very wide groups) they are collected already sorted;
 //   4. stage A: every 32-candidate chunk is tested against every query with
 //      an FP32 filter whose error band is certified; pairs inside the band
 //      are decided by the binary64 definition; one ballot per (query, chunk);
@@ -23,7 +25,9 @@
 //      when fused.
 // Groups whose candidate set exceeds the buffer, or spans too many original
 // indices for 32-bit sort keys, are processed in windows of original index
-// (same results, more passes).
+// (same results, more passes).  The same kernel also counts only (compressed
+// rows, first pass), writes rows at given offsets (second pass), and keeps
+// only j > i (half rows).
 #include "bt_internal.cuh"
 #include "bt_sort.cuh"
 #include "bt_find.cuh"

@@ -13,7 +13,7 @@ namespace bt {
 void note_launch(int k = 1);
 
 constexpr int kDepthMax = 32;   // a cell at depth 32 is never split
-constexpr int kGroupMax = 32;   // particles per find work unit
+constexpr int kGroupMax = 32;   // most particles per find work unit (per set: 1..32)
 constexpr int kWholeMax = 32;   // cells up to this size become one work unit
 constexpr int kSmallCap = 256;  // cells up to this size are built by one warp in smem
 constexpr int kBigChunk = 4096; // particles per block in the per-level big-cell passes
@@ -33,7 +33,6 @@ enum : uint32_t {
 
 // NodeWalk.flags
 enum : int {
-    kFlagLeaf = 1,         // a cell with > s particles that stayed a leaf
     kFlagWide = 2,         // FP32 fast path unusable: build uses FP64, walk visits all cells
     kFlagDegen0 = 4,       // zero width in dimension 0 (then 8, 16 for dims 1, 2)
 };
