@@ -34,6 +34,7 @@ struct GraphKey {
     float *smass, *rho;
     int32_t *nbrs, *counts;
     int ngmax, sms;
+    long long root_chunks;  // sets the grid of the root passes
 };
 
 
@@ -72,6 +73,8 @@ struct btree {
     // per-set tables (device) and their pinned host staging
     int nsets = 0, cap_sets = 0;
     int *set_start = nullptr, *set_s = nullptr, *set_na = nullptr, *set_gmax = nullptr;
+    int *set_chunk0 = nullptr;
+    long long root_chunks = 0;  // root-pass blocks over all sets
     int *set_flags = nullptr, *set_bbox = nullptr;
     double *set_beta = nullptr;
     SetRec *h_rec = nullptr;    // [cap_sets] mapped pinned staging, read by k_init_sets
@@ -148,7 +151,8 @@ void free_all(btree *t)
     t->cap_csr = 0;
     dev_free(t, t->set_start); dev_free(t, t->set_s); dev_free(t, t->set_na); dev_free(t, t->set_gmax);
     dev_free(t, t->set_flags); dev_free(t, t->set_bbox); dev_free(t, t->set_beta);
-    t->set_start = t->set_s = t->set_na = t->set_gmax = nullptr;
+    dev_free(t, t->set_chunk0);
+    t->set_start = t->set_s = t->set_na = t->set_gmax = t->set_chunk0 = nullptr;
     t->set_flags = t->set_bbox = nullptr;
     t->set_beta = nullptr;
     t->cap_sets = 0;
@@ -171,6 +175,7 @@ TreeDev view(const btree *t)
     T.set_na = t->set_na;
     T.set_beta = t->set_beta;
     T.set_gmax = t->set_gmax;
+    T.set_chunk0 = t->set_chunk0;
     T.set_flags = t->set_flags;
     T.set_bbox = t->set_bbox;
     T.geom = t->geom;
@@ -266,6 +271,7 @@ int ensure_set_caps(btree *t, int nsets)
     const int c = std::max(nsets, 1);
     if (!realloc_dev(t, t->set_start, 0, c + 1, false) || !realloc_dev(t, t->set_s, 0, c, false) ||
         !realloc_dev(t, t->set_na, 0, c, false) || !realloc_dev(t, t->set_gmax, 0, c, false) ||
+        !realloc_dev(t, t->set_chunk0, 0, c + 1, false) ||
         !realloc_dev(t, t->set_beta, 0, c, false) ||
         !realloc_dev(t, t->set_flags, 0, c, false) || !realloc_dev(t, t->set_bbox, 0, 6 * c, false))
         return BT_ERR_OOM;
@@ -326,10 +332,11 @@ void launch_build_head(btree *t, const TreeDev &T, const LevelBufs &L, cudaStrea
                        bool capture = false)
 {
     launch_init_counters(t->ctr, t->nsets, st);
-    launch_init_sets(T, t->h_rec_dev, t->set_start, t->set_s, t->set_na, t->set_beta, t->set_gmax, st);
+    launch_init_sets(T, t->h_rec_dev, t->set_start, t->set_s, t->set_na, t->set_beta, t->set_gmax,
+                     t->set_chunk0, st);
     record_event(t->ev0, st, capture);
-    launch_bbox(T, L.in.x, L.in.y, L.in.z, L.in.h, t->sms, st);
-    launch_roots(T, L, t->sms, st);
+    launch_bbox(T, L.in.x, L.in.y, L.in.z, L.in.h, t->root_chunks, t->sms, st);
+    launch_roots(T, L, t->root_chunks, t->sms, st);
 }
 
 // After the build (counters on the host): retry on capacity, info.
@@ -506,6 +513,7 @@ int run_graph_step(btree *t, const float *x, const float *y, const float *z, con
     K.counts = counts;
     K.ngmax = ngmax;
     K.sms = t->sms;
+    K.root_chunks = t->root_chunks;
     if (!t->gexec || std::memcmp(&K, &t->gkey, sizeof(GraphKey)) != 0) {
         cudaGraph_t g = nullptr;
         g_capturing = true;
@@ -635,7 +643,9 @@ static void stage_set(btree *t, int i, int64_t start, int64_t end, int s, double
     r.s = s;
     r.flags = flags;
     r.gmax = gmax;
-    r.pad = 0;
+    // sets are staged in order: the blocks of set i follow those of set i - 1
+    r.chunk0 = i == 0 ? 0 : (int)t->root_chunks;
+    t->root_chunks = r.chunk0 + (end - start + kRootChunk - 1) / kRootChunk;
     r.alpha = alpha;
     r.beta = beta;
 }

@@ -53,83 +53,64 @@ __device__ __forceinline__ int set_b0(const TreeDev &T, int set, int count)
 
 // ------------------------------------------------------------------ bbox
 // Per-set bounding boxes (Eq. 2 "bounds of the domain"), plus a check that
-// every coordinate and h is finite and h >= 0.  A warp whose 32 particles
-// belong to one set keeps running per-lane extrema for that set and reduces
-// them only when its set changes (so a single set costs one flush per warp);
-// a warp that straddles a set boundary updates per lane.
-__device__ __forceinline__ void bbox_flush(int set, float mn0, float mn1, float mn2, float mx0,
-                                           float mx1, float mx2, int *set_bbox)
-{
-    if (set < 0) return;  // warp-uniform
-    for (int o = 16; o > 0; o >>= 1) {
-        mn0 = fminf(mn0, __shfl_xor_sync(~0u, mn0, o));
-        mn1 = fminf(mn1, __shfl_xor_sync(~0u, mn1, o));
-        mn2 = fminf(mn2, __shfl_xor_sync(~0u, mn2, o));
-        mx0 = fmaxf(mx0, __shfl_xor_sync(~0u, mx0, o));
-        mx1 = fmaxf(mx1, __shfl_xor_sync(~0u, mx1, o));
-        mx2 = fmaxf(mx2, __shfl_xor_sync(~0u, mx2, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        int *bb = set_bbox + 6 * set;
-        atomicMin(&bb[0], float_to_ordered(mn0));
-        atomicMin(&bb[1], float_to_ordered(mn1));
-        atomicMin(&bb[2], float_to_ordered(mn2));
-        atomicMax(&bb[3], float_to_ordered(mx0));
-        atomicMax(&bb[4], float_to_ordered(mx1));
-        atomicMax(&bb[5], float_to_ordered(mx2));
-    }
-}
-
-__global__ void __launch_bounds__(256) k_bbox(const float *__restrict__ x,
+// every coordinate and h is finite and h >= 0.
+// One block per kRootChunk particles of one set: coalesced loads, a block
+// reduction, six atomics per block.
+__global__ void __launch_bounds__(256) k_bbox(TreeDev T, const float *__restrict__ x,
                                               const float *__restrict__ y,
                                               const float *__restrict__ z,
-                                              const float *__restrict__ h, int n,
-                                              const int *set_start, int nsets, int *set_bbox,
-                                              Counters *ctr)
+                                              const float *__restrict__ h)
 {
-    const int stride = gridDim.x * blockDim.x;
-    const int n_round = (n + 31) & ~31;  // whole warps iterate together
-    int cur = -1;
-    float mn0 = FLT_MAX, mn1 = FLT_MAX, mn2 = FLT_MAX;
-    float mx0 = -FLT_MAX, mx1 = -FLT_MAX, mx2 = -FLT_MAX;
+    __shared__ float red[6][8];
+    __shared__ int s_set;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int total = T.set_chunk0[T.nsets];
     bool bad = false;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
-        const bool v = i < n;
-        float a = 0.f, b = 0.f, c = 0.f, hh = 0.f;
-        int set = -1;
-        if (v) {
-            a = x[i]; b = y[i]; c = z[i]; hh = h[i];
-            set = nsets == 1 ? 0 : find_set(set_start, nsets, i);
-            bad |= !isfinite(a) || !isfinite(b) || !isfinite(c) || !isfinite(hh) || !(hh >= 0.0f);
+    for (int c = blockIdx.x; c < total; c += gridDim.x) {
+        __syncthreads();  // red / s_set of the previous block step
+        if (tid == 0) s_set = set_of_chunk(T.set_chunk0, T.nsets, c);
+        __syncthreads();
+        const int set = s_set;
+        const int p0 = T.set_start[set] + (c - T.set_chunk0[set]) * kRootChunk;
+        const int p1 = min(p0 + kRootChunk, T.set_start[set + 1]);
+        float v[6] = {FLT_MAX, FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
+        for (int p = p0 + tid; p < p1; p += blockDim.x) {
+            const float a = x[p], b = y[p], cc = z[p], hh = h[p];
+            bad |= !isfinite(a) || !isfinite(b) || !isfinite(cc) || !isfinite(hh) || !(hh >= 0.0f);
+            v[0] = fminf(v[0], a); v[1] = fminf(v[1], b); v[2] = fminf(v[2], cc);
+            v[3] = fmaxf(v[3], a); v[4] = fmaxf(v[4], b); v[5] = fmaxf(v[5], cc);
         }
-        const unsigned same = __match_any_sync(~0u, set);
-        if (same == 0xffffffffu) {
-            if (set != cur) {
-                bbox_flush(cur, mn0, mn1, mn2, mx0, mx1, mx2, set_bbox);
-                cur = set;
-                mn0 = mn1 = mn2 = FLT_MAX;
-                mx0 = mx1 = mx2 = -FLT_MAX;
+        for (int o = 16; o > 0; o >>= 1)
+            for (int k = 0; k < 6; k++) {
+                const float w = __shfl_xor_sync(~0u, v[k], o);
+                v[k] = k < 3 ? fminf(v[k], w) : fmaxf(v[k], w);
             }
-            mn0 = fminf(mn0, a); mn1 = fminf(mn1, b); mn2 = fminf(mn2, c);
-            mx0 = fmaxf(mx0, a); mx1 = fmaxf(mx1, b); mx2 = fmaxf(mx2, c);
-        } else if (set >= 0) {
-            int *bb = set_bbox + 6 * set;
-            atomicMin(&bb[0], float_to_ordered(a));
-            atomicMin(&bb[1], float_to_ordered(b));
-            atomicMin(&bb[2], float_to_ordered(c));
-            atomicMax(&bb[3], float_to_ordered(a));
-            atomicMax(&bb[4], float_to_ordered(b));
-            atomicMax(&bb[5], float_to_ordered(c));
+        if (lane == 0)
+            for (int k = 0; k < 6; k++) red[k][warp] = v[k];
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = blockDim.x >> 5;
+            for (int k = 0; k < 6; k++) {
+                float w = lane < nw ? red[k][lane] : (k < 3 ? FLT_MAX : -FLT_MAX);
+                for (int o = 4; o > 0; o >>= 1) {
+                    const float u = __shfl_xor_sync(~0u, w, o);
+                    w = k < 3 ? fminf(w, u) : fmaxf(w, u);
+                }
+                if (lane == 0) {
+                    int *bb = T.set_bbox + 6 * set + k;
+                    if (k < 3) atomicMin(bb, float_to_ordered(w));
+                    else atomicMax(bb, float_to_ordered(w));
+                }
+            }
         }
     }
-    bbox_flush(cur, mn0, mn1, mn2, mx0, mx1, mx2, set_bbox);
-    if (__any_sync(~0u, bad) && (threadIdx.x & 31) == 0) atomicOr(&ctr->status, kStNonfinite);
+    if (__any_sync(~0u, bad) && lane == 0) atomicOr(&T.ctr->status, kStNonfinite);
 }
 
 // Per-set tables from the staged records.  n_j <= alpha*s (binary64) is
 // n_j <= floor(alpha*s) for integer n_j.
 __global__ void k_init_sets(TreeDev T, const SetRec *rec, int *set_start, int *set_s, int *set_na,
-                            double *set_beta, int *set_gmax)
+                            double *set_beta, int *set_gmax, int *set_chunk0)
 {
     const int nsets = T.nsets;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsets; s += gridDim.x * blockDim.x) {
@@ -139,7 +120,11 @@ __global__ void k_init_sets(TreeDev T, const SetRec *rec, int *set_start, int *s
             T.set_bbox[6 * s + 3 + l] = INT_MIN;
         }
         set_start[s] = r.start;
-        if (s == nsets - 1) set_start[nsets] = r.end;
+        set_chunk0[s] = r.chunk0;
+        if (s == nsets - 1) {
+            set_start[nsets] = r.end;
+            set_chunk0[nsets] = r.chunk0 + (r.end - r.start + kRootChunk - 1) / kRootChunk;
+        }
         set_s[s] = r.s;
         const double under = __dmul_rn(r.alpha, (double)r.s);
         set_na[s] = under < 0.0 ? -1 : (under >= 2147483647.0 ? INT_MAX : (int)floor(under));
@@ -204,17 +189,23 @@ __global__ void k_root_sets(TreeDev T, LevelBufs L)
         root_set(T, s, L);
 }
 
-// Sets that are one leaf: their particles are final where they are.
+// Sets that are one leaf: their particles are final where they are (one
+// block per root-pass chunk; blocks of other sets return at once).
 __global__ void k_copy_leaf_roots(TreeDev T, const float *__restrict__ x, const float *__restrict__ y,
                                   const float *__restrict__ z, const float *__restrict__ h)
 {
     if (T.ctr->abort) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.n; i += gridDim.x * blockDim.x) {
-        const int s = T.nsets == 1 ? 0 : find_set(T.set_start, T.nsets, i);
-        if (!(T.set_flags[s] & kSetLeafRoot)) continue;
-        T.spos[i] = make_float4(x[i], y[i], z[i], __int_as_float(i));
-        T.sh[i] = h[i];
-        T.inv[i] = i;
+    const int total = T.set_chunk0[T.nsets];
+    for (int c = blockIdx.x; c < total; c += gridDim.x) {
+        const int set = set_of_chunk(T.set_chunk0, T.nsets, c);
+        if (!(T.set_flags[set] & kSetLeafRoot)) continue;  // uniform over the block
+        const int p0 = T.set_start[set] + (c - T.set_chunk0[set]) * kRootChunk;
+        const int p1 = min(p0 + kRootChunk, T.set_start[set + 1]);
+        for (int i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+            T.spos[i] = make_float4(x[i], y[i], z[i], __int_as_float(i));
+            T.sh[i] = h[i];
+            T.inv[i] = i;
+        }
     }
 }
 
@@ -1114,27 +1105,26 @@ static inline int grid_for(long long work, int per_block, int max_blocks)
 }
 
 void launch_init_sets(const TreeDev &T, const SetRec *rec, int *set_start, int *set_s, int *set_na,
-                      double *set_beta, int *set_gmax, cudaStream_t st)
+                      double *set_beta, int *set_gmax, int *set_chunk0, cudaStream_t st)
 {
     note_launch();
     k_init_sets<<<grid_for(T.nsets, 256, 1 << 16), 256, 0, st>>>(T, rec, set_start, set_s, set_na,
-                                                                 set_beta, set_gmax);
+                                                                 set_beta, set_gmax, set_chunk0);
 }
 
 void launch_bbox(const TreeDev &T, const float *x, const float *y, const float *z, const float *h,
-                 int sms, cudaStream_t st)
+                 long long chunks, int sms, cudaStream_t st)
 {
     note_launch();
-    k_bbox<<<grid_for(T.n, 256 * 8, sms * 8), 256, 0, st>>>(x, y, z, h, T.n, T.set_start, T.nsets,
-                                                             T.set_bbox, T.ctr);
+    k_bbox<<<grid_for(chunks, 1, sms * 8), 256, 0, st>>>(T, x, y, z, h);
 }
 
-void launch_roots(const TreeDev &T, const LevelBufs &L, int sms, cudaStream_t st)
+void launch_roots(const TreeDev &T, const LevelBufs &L, long long chunks, int sms, cudaStream_t st)
 {
     note_launch();
     k_root_sets<<<grid_for(T.nsets, 128, 1 << 16), 128, 0, st>>>(T, L);
     note_launch();
-    k_copy_leaf_roots<<<grid_for(T.n, 256, sms * 8), 256, 0, st>>>(T, L.in.x, L.in.y, L.in.z, L.in.h);
+    k_copy_leaf_roots<<<grid_for(chunks, 1, sms * 8), 256, 0, st>>>(T, L.in.x, L.in.y, L.in.z, L.in.h);
 }
 
 void launch_level_go(Counters *ctr, int advance, cudaGraphConditionalHandle h, int graph, cudaStream_t st)

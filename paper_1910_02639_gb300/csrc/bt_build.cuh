@@ -15,10 +15,10 @@ struct LevelHints {
 
 void launch_init_counters(Counters *ctr, int nroots, cudaStream_t st);
 void launch_init_sets(const TreeDev &T, const SetRec *rec, int *set_start, int *set_s, int *set_na,
-                      double *set_beta, int *set_gmax, cudaStream_t st);
+                      double *set_beta, int *set_gmax, int *set_chunk0, cudaStream_t st);
 void launch_bbox(const TreeDev &T, const float *x, const float *y, const float *z, const float *h,
-                 int sms, cudaStream_t st);
-void launch_roots(const TreeDev &T, const LevelBufs &L, int sms, cudaStream_t st);
+                 long long chunks, int sms, cudaStream_t st);
+void launch_roots(const TreeDev &T, const LevelBufs &L, long long chunks, int sms, cudaStream_t st);
 void launch_level_go(Counters *ctr, int advance, cudaGraphConditionalHandle h, int graph, cudaStream_t st);
 void launch_level_start(const TreeDev &T, const LevelBufs &L, const LevelHints &H, int sms,
                         cudaGraphConditionalHandle hratio, int graph, cudaStream_t st);

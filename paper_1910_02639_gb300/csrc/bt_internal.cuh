@@ -17,6 +17,7 @@ constexpr int kGroupMax = 32;   // most particles per find work unit (per set: 1
 constexpr int kWholeMax = 32;   // cells up to this size become one work unit
 constexpr int kSmallCap = 256;  // cells up to this size are built by one warp in smem
 constexpr int kBigChunk = 4096; // particles per block in the per-level big-cell passes
+constexpr int kRootChunk = 4096; // particles per block in the root passes (one set per block)
 
 // Status bits accumulated on the device (reported by btree_status).
 enum : uint32_t {
@@ -294,7 +295,7 @@ struct SetRec {
     int s;           // bucket size
     int flags;       // kSetOctree
     int gmax;        // particles per find work unit, 1..kGroupMax
-    int pad;
+    int chunk0;      // first kRootChunk-particle block of the set (root passes)
     double alpha, beta;  // Eq. 4
 };
 
@@ -322,6 +323,7 @@ struct TreeDev {
     const int *set_na;     // [nsets] largest n_j counted as underfull (alpha s, Eq. 4)
     const double *set_beta;  // [nsets] beta of Eq. 4
     const int *set_gmax;   // [nsets] particles per find work unit
+    const int *set_chunk0; // [nsets+1] first root-pass block of each set; [nsets] = all blocks
     int *set_flags;        // [nsets]
     int *set_bbox;         // [nsets][6] ordered-int min x,y,z, max x,y,z
     NodeGeom *geom;
@@ -346,6 +348,18 @@ __device__ __forceinline__ bool ratio_halves(const TreeDev &T, int set, int u, i
 {
     const double bb = (double)ncells(b, set_dim(T, set));
     return (double)u > __dmul_rn(T.set_beta[set], bb);
+}
+
+// The set of root-pass block c: the last set whose first block is <= c
+// (empty sets own no block and are skipped).
+__device__ __forceinline__ int set_of_chunk(const int *chunk0, int nsets, int c)
+{
+    int lo = 0, hi = nsets - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (chunk0[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
 
 // The set holding particle p (binary search over the set offsets).
