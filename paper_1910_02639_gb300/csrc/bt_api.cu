@@ -190,6 +190,8 @@ TreeDev view(const btree *t)
     T.cap_slots = t->cap_slots;
     T.cap_groups = t->cap_groups;
     T.cap_small = t->cap_small;
+    T.small_hist = small_hist_cells((int)std::max<int64_t>(t->s, 1));
+    T.pad_t = 0;
     return T;
 }
 

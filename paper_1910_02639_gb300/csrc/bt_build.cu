@@ -24,18 +24,47 @@
 #include "bt_build.cuh"
 
 #include <cfloat>
+#include <cooperative_groups.h>
+#include <cooperative_groups/scan.h>
 
 namespace bt {
 
+namespace cg = cooperative_groups;
+
+// atomicAdd(p, v) by the group's threads together: one atomic per group,
+// each thread gets the old value plus the sum of the values of the lower
+// ranks.  Every thread of the group passes the same p.
+template <class G>
+__device__ __forceinline__ int group_atomic_add(const G &g, int *p, int v)
+{
+    const int incl = cg::inclusive_scan(g, v);
+    int base = 0;
+    if (g.thread_rank() == g.num_threads() - 1) base = atomicAdd(p, incl);
+    return g.shfl(base, g.num_threads() - 1) + incl - v;
+}
+
+// The same for the threads of the warp that reach this call together.
+__device__ __forceinline__ int warp_atomic_add(int *p, int v)
+{
+    return group_atomic_add(cg::coalesced_threads(), p, v);
+}
+
 // Work units of at most the set's gmax particles over tree positions
 // [start, start + cnt).  Sets searched by the compact block shape fill the
-// groups array from its end, the others from its start.
+// groups array from its end, the others from its start.  kWarpAgg: the
+// threads that call together share one atomic per counter (the level
+// kernels, one thread per sub-cell); the per-warp small-cell builder calls
+// from one lane at a time and takes plain atomics.
+template <bool kWarpAgg = false>
 __device__ __forceinline__ void emit_groups(const TreeDev &T, int set, int start, int cnt)
 {
     const int gm = T.set_gmax[set];
     const int ng = (cnt + gm - 1) / gm;
     const bool compact = (T.set_flags[set] & kSetFindCompact) != 0;
-    const int g0 = atomicAdd(compact ? &T.ctr->ngroups_c : &T.ctr->ngroups, ng);
+    int *ctr = compact ? &T.ctr->ngroups_c : &T.ctr->ngroups;
+    const int g0 = kWarpAgg
+                       ? group_atomic_add(cg::labeled_partition(cg::coalesced_threads(), (int)compact), ctr, ng)
+                       : atomicAdd(ctr, ng);
     for (int q = 0; q < ng; q++) {
         if (g0 + q >= T.cap_groups) break;
         const int idx = compact ? T.cap_groups - 1 - (g0 + q) : g0 + q;
@@ -379,9 +408,17 @@ __device__ __forceinline__ int sub_cell_id(const float4 &p, const NodeWalk &w, c
     return c0 + b * (c1 + b * c2);
 }
 
-// Histogram pass of one candidate b for every pending big cell.
+// Histogram pass of one candidate b for every pending big cell.  A cell
+// with at most kPrivBins sub-cells is counted in shared memory first and
+// added to the global histogram once per non-empty bin and block: with few
+// bins, thousands of particles of a block would otherwise serialise on the
+// same few global counters.
+constexpr int kPrivBins = 4096;
+static_assert(kPrivBins <= 4096 && kBigChunk <= 4096, "sub-cell and rank packed in 12 bits each");
+
 __global__ void __launch_bounds__(256) k_big_hist(TreeDev T, LevelBufs L)
 {
+    __shared__ int sh_bin[kPrivBins];
     const Counters *ctr = T.ctr;
     if (ctr->abort) return;
     const int nb = ctr->nbig;
@@ -395,13 +432,28 @@ __global__ void __launch_bounds__(256) k_big_hist(TreeDev T, LevelBufs L)
         if (c.state != 0) continue;  // uniform across the block
         NodeGeom g;
         NodeWalk w;
-        block_cell_params(T, c, g, w);
+        block_cell_params(T, c, g, w);  // (begins with a block barrier)
         int p0 = g.start + (chunk - c.chunk_base) * kBigChunk;
         int p1 = min(p0 + kBigChunk, g.start + g.count);
         int *hc = hist + c.hist_base;
+        const int nc = ncells(c.b, set_dim(T, c.set));
+        if (nc > kPrivBins) {
+            for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+                float4 r = src.load_pos(p);
+                atomicAdd(&hc[sub_cell_id(r, w, g, c.b)], 1);
+            }
+            continue;
+        }
+        for (int j = threadIdx.x; j < nc; j += blockDim.x) sh_bin[j] = 0;
+        __syncthreads();
         for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
             float4 r = src.load_pos(p);
-            atomicAdd(&hc[sub_cell_id(r, w, g, c.b)], 1);
+            atomicAdd(&sh_bin[sub_cell_id(r, w, g, c.b)], 1);
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+            const int v = sh_bin[j];
+            if (v) atomicAdd(&hc[j], v);
         }
     }
 }
@@ -585,22 +637,22 @@ __global__ void __launch_bounds__(256) k_big_emit(TreeDev T, LevelBufs L)
         const int depth = g.depth + 1;
         int child = -1;
         if (cnt > s && depth < kDepthMax) {
-            child = atomicAdd(&T.ctr->nnodes, 1);
+            child = warp_atomic_add(&T.ctr->nnodes, 1);
             if (child >= T.cap_nodes) {
                 atomicOr(&T.ctr->status, kStCapNodes);
                 child = -1;
             } else {
-                NodeGeom cg;
+                NodeGeom ng;
                 int cc[3] = {j % b, (j / b) % b, j / (b * b)};
                 for (int l = 0; l < 3; l++)
-                    child_bounds_w(g.lo[l], g.hi[l], c.w[l], dim_b(b, kd, l), cc[l], cg.lo[l], cg.hi[l]);
-                cg.start = start;
-                cg.count = cnt;
-                cg.depth = depth;
-                cg.set = c.set;
-                T.geom[child] = cg;
+                    child_bounds_w(g.lo[l], g.hi[l], c.w[l], dim_b(b, kd, l), cc[l], ng.lo[l], ng.hi[l]);
+                ng.start = start;
+                ng.count = cnt;
+                ng.depth = depth;
+                ng.set = c.set;
+                T.geom[child] = ng;
                 if (cnt > kSmallCap) {
-                    const int k = atomicAdd(&T.ctr->nbig_next, 1);
+                    const int k = warp_atomic_add(&T.ctr->nbig_next, 1);
                     if (k < L.cap_big) {
                         next_big[k] = child;
                     } else {
@@ -608,7 +660,7 @@ __global__ void __launch_bounds__(256) k_big_emit(TreeDev T, LevelBufs L)
                         T.ctr->abort = 1;
                     }
                 } else {
-                    int k = atomicAdd(&T.ctr->nsmall, 1);
+                    int k = warp_atomic_add(&T.ctr->nsmall, 1);
                     if (k < T.cap_small) small[k] = SmallItem{child, dst_buf};
                     else atomicOr(&T.ctr->status, kStCapSmall);
                 }
@@ -619,7 +671,7 @@ __global__ void __launch_bounds__(256) k_big_emit(TreeDev T, LevelBufs L)
                 atomicOr(&T.ctr->status, kStOversized);
             }
             if (!(T.set_flags[c.set] & kSetPackLeaves)) {
-                emit_groups(T, c.set, start, cnt);
+                emit_groups<true>(T, c.set, start, cnt);
             } else {
                 // leaf sub-cells 2i and 2i+1 (adjacent in tree order) share
                 // a work unit when both are leaves and fit together
@@ -631,8 +683,8 @@ __global__ void __launch_bounds__(256) k_big_emit(TreeDev T, LevelBufs L)
                     const bool leafp = cp > 0 && !(cp > s && depth < kDepthMax);
                     paired = leafp && cnt + cp <= gm;
                 }
-                if (!paired) emit_groups(T, c.set, start, cnt);
-                else if ((j & 1) == 0) emit_groups(T, c.set, start, cnt + hist[c.hist_base + jp]);
+                if (!paired) emit_groups<true>(T, c.set, start, cnt);
+                else if ((j & 1) == 0) emit_groups<true>(T, c.set, start, cnt + hist[c.hist_base + jp]);
             }
         }
         T.slots[c.slot0 + j] = Slot{start, cnt, child, 0};
@@ -642,8 +694,27 @@ __global__ void __launch_bounds__(256) k_big_emit(TreeDev T, LevelBufs L)
 // Move every particle of an accepted big cell to its sub-cell.  Leaf
 // sub-cells are final: they go straight to tree order; others to the
 // working buffer `dst` for the next level / the warp builder.
+__device__ __forceinline__ void scatter_one(const TreeDev &T, const BigCell &c, int j, int pos,
+                                            const float4 &r, float hh, float4 *dst_pos, float *dst_h)
+{
+    if (T.slots[c.slot0 + j].child < 0) {  // a leaf: final position
+        T.spos[pos] = r;
+        T.sh[pos] = hh;
+        T.inv[__float_as_int(r.w)] = pos;
+    } else {
+        dst_pos[pos] = r;
+        dst_h[pos] = hh;
+    }
+}
+
+// Move every particle of the level's big cells to its sub-cell's range.  A
+// cell with at most kPrivBins sub-cells ranks the block's particles per
+// sub-cell in shared memory and reserves each sub-cell's run with one global
+// atomic (the order within a sub-cell is not part of any result).
 __global__ void __launch_bounds__(256) k_big_scatter(TreeDev T, LevelBufs L)
 {
+    __shared__ int sh_bin[kPrivBins];
+    __shared__ int sh_jr[kBigChunk];  // per particle: sub-cell << 12 | rank within the block
     const Counters *ctr = T.ctr;
     if (ctr->abort) return;
     const int nb = ctr->nbig;
@@ -658,29 +729,49 @@ __global__ void __launch_bounds__(256) k_big_scatter(TreeDev T, LevelBufs L)
         BigCell c = big[ci];
         NodeGeom g;
         NodeWalk w;
-        block_cell_params(T, c, g, w);
+        block_cell_params(T, c, g, w);  // (begins with a block barrier)
         int p0 = g.start + (chunk - c.chunk_base) * kBigChunk;
         int p1 = min(p0 + kBigChunk, g.start + g.count);
+        if (c.state == 2) {  // stayed a leaf: final where it is
+            for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+                float4 r;
+                float hh;
+                src.load(p, r, hh);
+                T.spos[p] = r;
+                T.sh[p] = hh;
+                T.inv[__float_as_int(r.w)] = p;
+            }
+            continue;
+        }
+        const int nc = ncells(c.b, set_dim(T, c.set));
+        if (nc > kPrivBins) {
+            for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+                float4 r;
+                float hh;
+                src.load(p, r, hh);
+                const int j = sub_cell_id(r, w, g, c.b);
+                scatter_one(T, c, j, atomicAdd(&cursor[c.hist_base + j], 1), r, hh, dst_pos, dst_h);
+            }
+            continue;
+        }
+        for (int j = threadIdx.x; j < nc; j += blockDim.x) sh_bin[j] = 0;
+        __syncthreads();
+        for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+            const int j = sub_cell_id(src.load_pos(p), w, g, c.b);
+            sh_jr[p - p0] = j << 12 | atomicAdd(&sh_bin[j], 1);
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+            const int v = sh_bin[j];
+            if (v) sh_bin[j] = atomicAdd(&cursor[c.hist_base + j], v);
+        }
+        __syncthreads();
         for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
             float4 r;
             float hh;
             src.load(p, r, hh);
-            if (c.state == 2) {  // stayed a leaf: final where it is
-                T.spos[p] = r;
-                T.sh[p] = hh;
-                T.inv[__float_as_int(r.w)] = p;
-                continue;
-            }
-            int j = sub_cell_id(r, w, g, c.b);
-            int pos = atomicAdd(&cursor[c.hist_base + j], 1);
-            if (T.slots[c.slot0 + j].child < 0) {
-                T.spos[pos] = r;
-                T.sh[pos] = hh;
-                T.inv[__float_as_int(r.w)] = pos;
-            } else {
-                dst_pos[pos] = r;
-                dst_h[pos] = hh;
-            }
+            const int jr = sh_jr[p - p0], j = jr >> 12;
+            scatter_one(T, c, j, sh_bin[j] + (jr & 4095), r, hh, dst_pos, dst_h);
         }
     }
 }
@@ -791,18 +882,35 @@ struct Frame {
 };
 
 constexpr int kSmallWarps = 4;
-constexpr int kHistMax = 512;  // >= b0^3 for any cell of <= kSmallCap particles
+constexpr int kHistMax = 512;  // >= b0^k for any cell of <= kSmallCap particles and s >= 1
+static_assert(kSmallCap % 32 == 0, "whole particles per lane");
 
+// Per warp; the warps' histograms (2 x T.small_hist ints each: counts and
+// offsets) follow the kSmallWarps records.
 struct SmallSmem {
-    float4 p[2][kSmallCap];
-    float h[2][kSmallCap];
+    float x[kSmallCap], y[kSmallCap], z[kSmallCap];  // one array per field, so that
+    int id[kSmallCap];                                 // the in-place scatter moves one
+    float h[kSmallCap];                                // field at a time
     short key[kSmallCap];
-    int hist[kHistMax];
-    int off[kHistMax];
     Frame fr[kDepthMax + 2];
     NodeWalk w;
-    int scal[4];
 };
+
+// v[pos[k]] = v[k] for k < m (pos a permutation of 0..m-1), in place: each
+// lane holds its (at most kSmallCap / 32) values in registers meanwhile.
+template <class V>
+__device__ __forceinline__ void permute_field(V *v, const short *pos, int m, int lane)
+{
+    V r[kSmallCap / 32];
+#pragma unroll
+    for (int q = 0; q < kSmallCap / 32; q++)
+        if (lane + 32 * q < m) r[q] = v[lane + 32 * q];
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < kSmallCap / 32; q++)
+        if (lane + 32 * q < m) v[pos[lane + 32 * q]] = r[q];
+    __syncwarp();
+}
 
 __device__ __forceinline__ int warp_sum(int v)
 {
@@ -811,18 +919,26 @@ __device__ __forceinline__ int warp_sum(int v)
 }
 
 // One warp builds the whole sub-tree of one cell of <= kSmallCap particles.
-__global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const SmallItem *items,
+__global__ void __launch_bounds__(32 * kSmallWarps, 4) k_small(TreeDev T, const SmallItem *items,
                                                             Src src0, Src src1, Src srcin)
 {
     if (T.ctr->abort) return;
     const int nitems = min(T.ctr->nsmall, T.cap_small);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmallSmem &S = reinterpret_cast<SmallSmem *>(smem_raw)[threadIdx.x >> 5];
+    const int wid = threadIdx.x >> 5;
+    SmallSmem &S = reinterpret_cast<SmallSmem *>(smem_raw)[wid];
+    int *const hist = reinterpret_cast<int *>(smem_raw + kSmallWarps * sizeof(SmallSmem)) +
+                      wid * 2 * T.small_hist;
+    int *const off = hist + T.small_hist;
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * kSmallWarps + (threadIdx.x >> 5);
-    const int nw = gridDim.x * kSmallWarps;
 
-    for (int it = gw; it < nitems; it += nw) {
+    // cells are taken one at a time from a shared counter (their costs differ
+    // widely), by a grid of as many warps as are resident
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(&T.ctr->small_next, 1);
+        it = __shfl_sync(~0u, it, 0);
+        if (it >= nitems) break;
         const SmallItem item = items[it];
         const NodeGeom G = T.geom[item.node];
         const int base = G.start, m0 = G.count;
@@ -832,13 +948,16 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
         const bool octree = (T.set_flags[set] & kSetOctree) != 0;
         const bool pack = (T.set_flags[set] & kSetPackLeaves) != 0;
         const int kd = set_dim(T, set);
-        const Src &src = item.src == 0 ? src0 : (item.src == 1 ? src1 : srcin);
+        const Src src = item.src == 0 ? src0 : (item.src == 1 ? src1 : srcin);
         for (int k = lane; k < m0; k += 32) {
             float4 r;
             float hh;
             src.load(base + k, r, hh);
-            S.p[0][k] = r;
-            S.h[0][k] = hh;
+            S.x[k] = r.x;
+            S.y[k] = r.y;
+            S.z[k] = r.z;
+            S.id[k] = __float_as_int(r.w);
+            S.h[k] = hh;
         }
         if (lane == 0) {
             Frame &f = S.fr[0];
@@ -864,16 +983,16 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                     __syncwarp();
                     const NodeWalk w = S.w;
                     const int ncell = ncells(b, kd);
-                    for (int j = lane; j < ncell; j += 32) S.hist[j] = 0;
+                    for (int j = lane; j < ncell; j += 32) hist[j] = 0;
                     __syncwarp();
                     for (int k = lane; k < m; k += 32) {
-                        int j = sub_cell_id(S.p[0][a + k], w, g, b);
+                        int j = sub_cell_id(make_float4(S.x[a + k], S.y[a + k], S.z[a + k], 0.0f), w, g, b);
                         S.key[a + k] = (short)j;
-                        atomicAdd(&S.hist[j], 1);
+                        atomicAdd(&hist[j], 1);
                     }
                     __syncwarp();
                     int u = 0;
-                    for (int j = lane; j < ncell; j += 32) u += S.hist[j] <= na;
+                    for (int j = lane; j < ncell; j += 32) u += hist[j] <= na;
                     u = warp_sum(u);
                     if (b > 2 && ratio_halves(T, set, u, b)) {
                         b = max(2, b / 2);
@@ -889,7 +1008,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                 // no-progress guard
                 int ne = 0, lj = -1;
                 for (int j = lane; j < ncell; j += 32)
-                    if (S.hist[j] > 0) { ne++; lj = j; }
+                    if (hist[j] > 0) { ne++; lj = j; }
                 ne = warp_sum(ne);
                 for (int o = 16; o > 0; o >>= 1) lj = max(lj, __shfl_xor_sync(~0u, lj, o));
                 bool leaf = false;
@@ -922,13 +1041,13 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                     int carry = 0;
                     for (int j0 = 0; j0 < ncell; j0 += 32) {
                         int j = j0 + lane;
-                        int v = j < ncell ? S.hist[j] : 0;
+                        int v = j < ncell ? hist[j] : 0;
                         int incl = v;
                         for (int o = 1; o < 32; o <<= 1) {
                             int t = __shfl_up_sync(~0u, incl, o);
                             if (lane >= o) incl += t;
                         }
-                        if (j < ncell) S.off[j] = carry + incl - v;
+                        if (j < ncell) off[j] = carry + incl - v;
                         carry += __shfl_sync(~0u, incl, 31);
                     }
                 }
@@ -942,7 +1061,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                         // middle (sub-cell ids run x fastest: low ids are low z)
                         int bnd = 0, best = m;
                         for (int j = 0; j <= ncell; j++) {
-                            const int o = j < ncell ? S.off[j] : m;
+                            const int o = j < ncell ? off[j] : m;
                             const int d = abs(2 * o - m);
                             if (d < best) { best = d; bnd = o; }
                         }
@@ -969,8 +1088,8 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                     break;
                 }
                 for (int j = lane; j < ncell; j += 32) {
-                    const int cnt = S.hist[j];
-                    const int start = base + a + S.off[j];
+                    const int cnt = hist[j];
+                    const int start = base + a + off[j];
                     const int depth = F.depth + 1;
                     int child = -1;
                     if (cnt > s_set && depth < kDepthMax) {
@@ -1004,9 +1123,9 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                     const int depth = F.depth + 1;
                     int ps = 0, pc = 0, prow = -1;
                     for (int j = 0; j < ncell; j++) {
-                        const int cnt = S.hist[j];
+                        const int cnt = hist[j];
                         if (cnt == 0) continue;
-                        const int start = base + a + S.off[j];
+                        const int start = base + a + off[j];
                         if (cnt > s_set && depth < kDepthMax) {  // an internal sub-cell
                             if (pc > 0) emit_groups(T, set, ps, pc);
                             pc = 0;
@@ -1031,20 +1150,18 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
                     T.walk[F.node] = w;
                     atomicMax(&T.ctr->max_depth, F.depth + 1);
                 }
-                // scatter within shared memory, then copy back
-                for (int j = lane; j < ncell; j += 32) S.hist[j] = S.off[j];
+                // scatter in place: every lane holds its particles in
+                // registers while their new positions are taken
+                for (int j = lane; j < ncell; j += 32) hist[j] = off[j];
                 __syncwarp();
-                for (int k = lane; k < m; k += 32) {
-                    int j = S.key[a + k];
-                    int pos = atomicAdd(&S.hist[j], 1);
-                    S.p[1][a + pos] = S.p[0][a + k];
-                    S.h[1][a + pos] = S.h[0][a + k];
-                }
+                for (int k = lane; k < m; k += 32)
+                    S.key[a + k] = (short)atomicAdd(&hist[S.key[a + k]], 1);  // now the position
                 __syncwarp();
-                for (int k = lane; k < m; k += 32) {
-                    S.p[0][a + k] = S.p[1][a + k];
-                    S.h[0][a + k] = S.h[1][a + k];
-                }
+                permute_field(S.x + a, S.key + a, m, lane);
+                permute_field(S.y + a, S.key + a, m, lane);
+                permute_field(S.z + a, S.key + a, m, lane);
+                permute_field(S.h + a, S.key + a, m, lane);
+                permute_field(S.id + a, S.key + a, m, lane);
                 if (lane == 0) { F.b = b; F.slot0 = slot0; F.next = 0; }
                 __syncwarp();
             } else {
@@ -1084,16 +1201,19 @@ __global__ void __launch_bounds__(32 * kSmallWarps) k_small(TreeDev T, const Sma
         }
         __syncwarp();
         for (int k = lane; k < m0; k += 32) {
-            float4 r = S.p[0][k];
-            T.spos[base + k] = r;
-            T.sh[base + k] = S.h[0][k];
-            T.inv[__float_as_int(r.w)] = base + k;
+            const int id = S.id[k];
+            T.spos[base + k] = make_float4(S.x[k], S.y[k], S.z[k], __int_as_float(id));
+            T.sh[base + k] = S.h[k];
+            T.inv[id] = base + k;
         }
         __syncwarp();
     }
 }
 
-size_t small_smem_bytes() { return sizeof(SmallSmem) * kSmallWarps; }
+size_t small_smem_bytes(int hist_cells)
+{
+    return (sizeof(SmallSmem) + 2 * sizeof(int) * (size_t)hist_cells) * kSmallWarps;
+}
 
 // ------------------------------------------------------------------ host side
 static inline int grid_for(long long work, int per_block, int max_blocks)
@@ -1191,15 +1311,31 @@ void launch_small(const TreeDev &T, const LevelBufs &L, long long nitems_hint, i
     if (nitems_hint <= 0) return;
     const Src s0{nullptr, nullptr, nullptr, nullptr, L.wpos[0], L.wh[0]};
     const Src s1{nullptr, nullptr, nullptr, nullptr, L.wpos[1], L.wh[1]};
-    int blocks = grid_for(nitems_hint, kSmallWarps, sms * 4);
+    const size_t smem = small_smem_bytes(T.small_hist);
+    // as many blocks as are resident at once (the warps take cells from a
+    // counter until none is left)
+    static thread_local size_t occ_smem = 0;
+    static thread_local int occ_blocks = 0;
+    if (occ_smem != smem) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small, 32 * kSmallWarps, smem) !=
+                cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        occ_smem = smem;
+        occ_blocks = per_sm;
+    }
+    const int blocks = grid_for(nitems_hint, kSmallWarps, sms * occ_blocks);
     note_launch();
-    k_small<<<blocks, 32 * kSmallWarps, small_smem_bytes(), st>>>(T, L.small, s0, s1, L.in);
+    k_small<<<blocks, 32 * kSmallWarps, smem, st>>>(T, L.small, s0, s1, L.in);
 }
 
 cudaError_t build_init_attributes()
 {
     return cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)small_smem_bytes());
+                                (int)small_smem_bytes(kHistMax));
 }
 
 // One thread: copy the counters (and node 0's b) into the mapped host mirror.

@@ -29,7 +29,7 @@ void launch_level_finish(const TreeDev &T, const LevelBufs &L, const LevelHints 
                          cudaGraphConditionalHandle hlevel, int graph, cudaStream_t st);
 void launch_small(const TreeDev &T, const LevelBufs &L, long long nitems_hint, int sms, cudaStream_t st);
 int scan_tile_count(long long n);
-size_t small_smem_bytes();
+size_t small_smem_bytes(int hist_cells);
 // Small read-backs into mapped pinned host memory (see Readback).
 void launch_readback(const Counters *ctr, const NodeWalk *walk0, Readback *out, cudaStream_t st);
 void launch_readback_total(const long long *total, Readback *out, cudaStream_t st);

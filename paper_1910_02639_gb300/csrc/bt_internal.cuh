@@ -262,7 +262,7 @@ struct Counters {
     int abort;         // capacity or input problem: the remaining kernels do nothing
     long long hist_need;  // histogram entries a level asked for (on abort)
     int ngroups_c;     // work units of the compact-shape list (end of the groups array)
-    int pad_c;
+    int small_next;    // dynamic work counter of the warp builder
 };
 
 // Per big cell of the current level.
@@ -335,7 +335,20 @@ struct TreeDev {
     int *inv;       // inverse permutation: tree position of original index
     Counters *ctr;
     int cap_nodes, cap_slots, cap_groups, cap_small;
+    int small_hist;  // histogram entries per warp of the small-cell builder (>= b0^k at kSmallCap)
+    int pad_t;
 };
+
+// Largest b^k that any cell of at most kSmallCap particles starts from, over
+// sets whose bucket size is at least smin (Eq. 1 is monotone in n and in 1/s;
+// the ratio test only lowers b).
+__host__ __device__ __forceinline__ int small_hist_cells(int smin)
+{
+    int c = ncells(branching_factor(kSmallCap, smin), 3);
+    c = c > ncells(branching_factor2(kSmallCap, smin), 2) ? c : ncells(branching_factor2(kSmallCap, smin), 2);
+    c = c > 8 ? c : 8;  // octree
+    return (c + 3) & ~3;
+}
 
 // Ratio test of Eq. 4 for a cell of the given set: halve b iff
 // u > beta * b^k, in binary64 (b^k is exact; u is an integer).
