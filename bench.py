@@ -372,6 +372,12 @@ def run_gpu(args):
                                          "workload) over the event-timed launch; peak = 152 SMs x 4 "
                                          "schedulers x SM clock"}
 
+    # ---- the device's FMA rates: why the distance test filters in FP32
+    if rank == 0:
+        r = bt.btree_arith_rates(stream)
+        out["arith_rates"] = {k: round(v, 1) for k, v in r.items()}
+        out["arith_rates"]["fp64_over_fp32"] = round(r["fp64_gflops"] / r["fp32_gflops"], 4)
+
     # ---- many uneven sets: batched vs the plain per-set path
     if not args.no_batched:
         out["batched"] = run_batched_section(args, bt, dev, stream, dist, rank, ws)

@@ -347,6 +347,17 @@ const char *btree_version(void);
  * is the number of kernel launches the region made. */
 uint64_t btree_kernel_launches(void);
 
+/* Measured arithmetic rates of the current device, in GFLOP/s (an FMA counts
+ * as 2): scalar FP32 FMA, packed FP32x2 FMA, and binary64 FMA, each from a
+ * kernel of independent FMA chains on every SM, timed with events on
+ * `stream` after a warm-up launch.  They justify the FP32 distance filter
+ * with binary64 only in its uncertain band (the distance test of Algorithm 2
+ * would be ALU-bound in binary64).  Any output pointer may be NULL.  Takes
+ * a few milliseconds and synchronises `stream`.  BT_ERR_CUDA on a launch or
+ * timing failure. */
+int btree_arith_rates(void *stream, double *fp32_gflops, double *fp32x2_gflops,
+                      double *fp64_gflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,6 +22,7 @@ __all__ = [
     "btree_find_neighbors_density", "btree_find_neighbors_density_noalloc",
     "btree_noalloc_max_particles", "sph_density", "btree_status", "btree_get_info",
     "btree_export", "btree_free", "btree_strerror", "btree_version", "btree_kernel_launches",
+    "btree_arith_rates",
     "library_path",
     "BT_OK", "BT_WARN_NGMAX", "BT_WARN_OVERSIZED_LEAF",
 ]
@@ -111,6 +112,9 @@ def _load():
         lib.btree_version.argtypes = []
         lib.btree_kernel_launches.restype = ctypes.c_uint64
         lib.btree_kernel_launches.argtypes = []
+        lib.btree_arith_rates.restype = ctypes.c_int
+        lib.btree_arith_rates.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                          ctypes.POINTER(dbl)]
         _lib = lib
         return lib
 
@@ -420,3 +424,12 @@ def btree_version() -> str:
 def btree_kernel_launches() -> int:
     """CUDA kernels launched by the library so far in this process."""
     return int(_load().btree_kernel_launches())
+
+
+def btree_arith_rates(stream=None) -> dict:
+    """Measured FMA throughput of the current device in GFLOP/s: scalar FP32,
+    packed FP32x2 and binary64 (see btree.h)."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_load().btree_arith_rates(ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(a),
+                                     ctypes.byref(b), ctypes.byref(c)), "btree_arith_rates")
+    return {"fp32_gflops": a.value, "fp32x2_gflops": b.value, "fp64_gflops": c.value}

@@ -652,6 +652,91 @@ static void stage_set(btree *t, int i, int64_t start, int64_t end, int s, double
     r.beta = beta;
 }
 
+// ------------------------------------------------------------------ arithmetic rates
+namespace bt {
+
+constexpr int kRateChains = 8;  // independent FMA chains per thread
+
+__device__ __forceinline__ float rate_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double rate_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ unsigned long long rate_fma(unsigned long long a, unsigned long long b,
+                                                       unsigned long long c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+template <class V>
+__global__ void __launch_bounds__(256) k_fma_rate(V *sink, int iters, V b, V c, V a0)
+{
+    V a[kRateChains];
+#pragma unroll
+    for (int k = 0; k < kRateChains; k++) a[k] = a0;
+    for (int i = 0; i < iters; i++)
+#pragma unroll
+        for (int k = 0; k < kRateChains; k++) a[k] = rate_fma(a[k], b, c);
+    bool keep = false;
+#pragma unroll
+    for (int k = 0; k < kRateChains; k++) keep |= a[k] == b;  // never true: keeps the chains live
+    if (keep) sink[threadIdx.x] = a[0];
+}
+
+template <class V>
+static cudaError_t time_rate(cudaStream_t st, int sms, int iters, V b, V c, V a0, double flops_per_fma,
+                             double *gflops)
+{
+    V *sink = nullptr;
+    cudaError_t e = cudaMalloc(&sink, 256 * sizeof(V));
+    if (e != cudaSuccess) return e;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks = sms * 8;
+    note_launch();
+    k_fma_rate<V><<<blocks, 256, 0, st>>>(sink, iters / 8, b, c, a0);  // warm-up
+    cudaEventRecord(e0, st);
+    note_launch();
+    k_fma_rate<V><<<blocks, 256, 0, st>>>(sink, iters, b, c, a0);
+    cudaEventRecord(e1, st);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && gflops)
+        *gflops = flops_per_fma * kRateChains * (double)iters * blocks * 256 / (ms * 1e6);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    return e;
+}
+
+static unsigned long long pack2(float f)
+{
+    unsigned u;
+    std::memcpy(&u, &f, sizeof(u));
+    return ((unsigned long long)u << 32) | u;
+}
+
+static int arith_rates(cudaStream_t st, double *fp32, double *fp32x2, double *fp64)
+{
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = time_rate<float>(st, sms, 16384, 0.9999999f, 1e-7f, 1.0f, 2.0, fp32);
+    if (e == cudaSuccess) {
+        e = time_rate<unsigned long long>(st, sms, 16384, pack2(0.9999999f), pack2(1e-7f), pack2(1.0f), 4.0,
+                                          fp32x2);
+    }
+    if (e == cudaSuccess) e = time_rate<double>(st, sms, 512, 0.9999999999, 1e-12, 1.0, 2.0, fp64);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return BT_ERR_CUDA;
+    }
+    return BT_OK;
+}
+
+}  // namespace bt
+
 extern "C" {
 
 int btree_build(const float *x, const float *y, const float *z, const float *h, int64_t n,
@@ -1002,6 +1087,11 @@ const char *btree_strerror(int status)
 }
 
 const char *btree_version(void) { return "btree-gb300 0.1 (sm_103a)"; }
+
+int btree_arith_rates(void *stream, double *fp32_gflops, double *fp32x2_gflops, double *fp64_gflops)
+{
+    return bt::arith_rates(static_cast<cudaStream_t>(stream), fp32_gflops, fp32x2_gflops, fp64_gflops);
+}
 
 uint64_t btree_kernel_launches(void) { return bt::g_launches.load(std::memory_order_relaxed); }
 

@@ -360,5 +360,62 @@ def test_slab_1e7_sampled(bt, gpu, oracle):
     gx, gy, gz = ix % 400, (ix // 400) % 250, ix // 100000
     inner = (gx > 5) & (gx < 394) & (gy > 5) & (gy < 244) & (gz > 5) & (gz < 94)
     assert abs(r["cnt"][inner].mean() - _jittered_lattice_mean_count(0.1, 3.0)) < 0.15
-    del r
+    # the headline launch configuration (one-set batched build, compact find
+    # shape) gives the same rows, counts and density bits on every particle
+    x, y, z, h, m = gpu.to_dev(s)
+    t2 = bt.btree_build_batched(x, y, z, h, np.array([0, s.n], np.int64),
+                                [dict(bucket_size=16, alpha=0.5, beta=0.5, find_compact=True)])
+    nb2 = torch.full_like(r["nb_dev"], -1)
+    cnt2 = torch.empty_like(r["cnt_dev"])
+    rho2 = torch.empty_like(r["rho_dev"])
+    bt.btree_find_neighbors_density(t2, m, 256, nb2, cnt2, rho2)
+    torch.cuda.synchronize()
+    assert torch.equal(cnt2, r["cnt_dev"])
+    assert torch.equal(nb2, r["nb_dev"])
+    assert torch.equal(rho2.view(torch.int32), r["rho_dev"].view(torch.int32))
+    t2.free()
+    del r, nb2
     torch.cuda.empty_cache()
+
+
+@pytest.mark.slow
+def test_batched_256_sets_sampled(bt, oracle):
+    """The 256-set workload at full size (35.6 M particles) as one CUDA-graph
+    launch, every tuning knob in use across the sets: sampled rows, counts and
+    densities of every set against the oracle tree of that set."""
+    import torch
+    from paper_1910_02639_gb300.batch import DeviceSets
+    sets = wl.batched_sets(256, seed=1914)
+    knobs = [dict(), dict(find_compact=True), dict(bucket_size=8, pack_leaves=True),
+             dict(bucket_size=64, beta=0.75, group_size=16), dict(bucket_size=32, beta=0.25)]
+    params = [knobs[i % len(knobs)] for i in range(len(sets))]
+    ds = DeviceSets(sets, "cuda:0", 256)
+    ds.run_graph(params)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    for i, s in enumerate(sets):
+        a = int(ds.offsets[i])
+        p = {**dict(bucket_size=16, beta=0.5), **params[i]}
+        ot = oracle.OracleTree(s.x, s.y, s.z, bucket_size=p["bucket_size"], beta=p["beta"])
+        for q in rng.choice(s.n, min(3, s.n), replace=False):
+            q = int(q)
+            ref_nb, ref_cnt = ot.find(s.h, 256, q, q + 1)
+            row = ds.nb[(a + q) * 256:(a + q + 1) * 256].cpu().numpy()
+            c = int(ds.cnt[a + q].item())
+            assert c == int(ref_cnt[0]), f"set {i} particle {q}: count {c} != {ref_cnt[0]}"
+            k = min(c, 256)
+            assert np.array_equal(row[:k], ref_nb[0, :k]), f"set {i} particle {q}: row differs"
+            ref_rho = ot.density(s.h, s.m, q, q + 1)[0]
+            assert abs(float(ds.rho[a + q].item()) - ref_rho) / ref_rho < DENS_TOL
+    ds.free()
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.gpu
+def test_arith_rates_measured():
+    """The FMA-rate diagnostic runs and orders the rates as the FP32 filter
+    assumes: binary64 far below FP32."""
+    import paper_1910_02639_gb300 as bt
+    r = bt.btree_arith_rates()
+    assert r["fp32_gflops"] > 1e3 and r["fp32x2_gflops"] > 1e3 and r["fp64_gflops"] > 10
+    assert r["fp64_gflops"] < 0.5 * r["fp32_gflops"]
