@@ -450,6 +450,15 @@ def run_e2e(args, bt, s, cfg, dev, stream, dist, ws, pairs, params):
     for k in range(2):
         step(k)
     torch.cuda.synchronize(dev)
+    # this box's device-to-host rate into pinned memory (explains the e2e time)
+    nl = min(cap, 1 << 28)
+    el0, el1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(copy_st):
+        el0.record(copy_st)
+        h_csr[0][:nl].copy_(csr[0][:nl], non_blocking=True)
+        el1.record(copy_st)
+    el1.synchronize()
+    d2h_gbs = 4.0 * nl / (el0.elapsed_time(el1) * 1e-3) / 1e9
     K = max(1, min(args.steps, args.e2e_steps))
     totals.clear()
     barrier(dist, dev)
@@ -468,6 +477,7 @@ def run_e2e(args, bt, s, cfg, dev, stream, dist, ws, pairs, params):
             "d2h_bytes_per_step": int(4 * tot + 8 * (n + 1) + 4 * n),
             "result": "compressed rows (every neighbour, ascending) + offsets + densities",
             "overlap": "copy-back of step k overlaps step k+1 (two output buffers)",
+            "d2h_gbs_measured": round(d2h_gbs, 1),
             "complete": bool(ok)}
 
 
