@@ -187,17 +187,6 @@ __device__ __forceinline__ void child_bounds_w(double lo, double hi, double w, i
     chi = (c == b - 1) ? hi : __dadd_rn(lo, __dmul_rn((double)(c + 1), w));
 }
 
-__device__ __forceinline__ void child_bounds(double lo, double hi, int b, int c,
-                                             double &clo, double &chi)
-{
-    child_bounds_w(lo, hi, cell_width(lo, hi, b), b, c, clo, chi);
-}
-
-// Largest number of underfull sub-cells at which branching factor b is
-// accepted (Eq. 4: halve iff u > beta*b^3 in binary64), tabulated per b on
-// the host for the tree's beta.
-constexpr int kMaxB = 1300;
-
 // Eq. 1 in integers: smallest b >= 2 with b^3 s >= n.  A float cube root
 // gives the starting point, exact integer tests settle it (no binary64 math:
 // it is slow on this GPU).
@@ -249,7 +238,6 @@ struct Counters {
     int noversized;
     int bbox[6];       // ordered-int min x,y,z then max x,y,z
     unsigned status;
-    int find_next;     // dynamic work counter of the find kernels
     int hist_total;    // sum of b0^3 over this level's big cells
     int chunk_total;   // blocks of kBigChunk particles over this level's big cells
     int level;         // big-cell level being built (0 = the set roots)
