@@ -97,6 +97,23 @@ def test_batched_equals_each_set_alone(bt):
         _assert_same(res[i], alone, "set %d (%s, n=%d)" % (i, s.name, s.n))
 
 
+def test_empty_sets_at_both_ends_and_chunk_boundaries(bt):
+    """Empty sets first, last and in a row; sets whose sizes straddle the
+    4096-particle blocks of the root passes (bounding box, one-leaf sets)."""
+    empty = wl._pack(np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0))
+    sets = [empty, empty, wl.uniform_cube(4096, seed=521, target=40), empty,
+            wl.uniform_cube(4097, seed=522, target=40), wl.uniform_cube(12, seed=523, target=8),
+            wl.evrard(8191, seed=524, target=50), empty, empty]
+    tree, off, res = run_batched(bt, sets)
+    tree.free()
+    for i, s in enumerate(sets):
+        if s.n == 0:
+            continue
+        alone = run_gpu(s, bucket_size=16, ngmax=NGMAX, density=True)
+        alone["tree"].free()
+        _assert_same(res[i], alone, "set %d (n=%d)" % (i, s.n))
+
+
 def test_batched_trees_match_the_oracle_per_set(bt, oracle):
     sets = _mixed_sets()
     params = [dict(bucket_size=(16, 5, 1, 8)[i % 4], beta=(0.5, 0.0, 1.0)[i % 3],
