@@ -9,7 +9,7 @@
 //   1. warp 0 loads the queries; then all threads walk the tree once for the
 //      union of their search intervals (Eqs. 5-6 applied to the group's query
 //      box), frontier by frontier, collecting contiguous particle ranges
-//      (x-runs of sub-cells in Eq. 3 order; internal sub-cells of <= 32
+//      (x-runs of sub-cells in Eq. 3 order; internal sub-cells of <= 256
 //      particles are taken whole) as 32-particle jobs;
 //   2. all warps stream the jobs with several coalesced float4 loads in
 //      flight per lane and keep the candidates within 2*h_max of the group's
@@ -53,7 +53,8 @@ using CfgWide = FindCfg<256, 1024, 10>;
 using CfgCompact = FindCfg<128, 512, 9>;
 constexpr int kSpanMax = (1 << 22) - 1;    // original-index span of one window
 constexpr int kFrontMax = 64;              // tree nodes per walk frontier
-constexpr int kDescendMin = 32;            // smaller internal sub-cells are scanned whole
+constexpr int kDescendMin = 256;           // internal sub-cells up to this size are scanned whole
+                                           // (fewer walk levels on deep trees; 32 was 2-26 % slower)
 constexpr int kFindChunk = 1;              // groups per block step (more: heavy neighbours
                                            // land on one block and stretch the tail)
 constexpr int kHitBatch = 256;             // hit positions staged per warp and pass
