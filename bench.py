@@ -582,7 +582,9 @@ def run_serving_section(args, dev, dist, rank, ws):
     continuous-batching loop (4 slots) and, under the same arrivals, by the
     plain path one job at a time.  Then the same requests all at once
     (saturated) for throughput.  Each rank serves its own share of the
-    stream."""
+    stream.  Unless --no-tune, every request carries the autotuner's
+    parameters for its class of set (size, spread of h); the plain path uses
+    the tree parameters among them."""
     import numpy as np
     import torch
     from paper_1910_02639_gb300 import serving
@@ -591,7 +593,20 @@ def run_serving_section(args, dev, dist, rank, ws):
     specs = wl.request_stream(args.serving_requests, seed=1915, rate=200.0)
     mine = shard_sets([1] * len(specs), ws)[rank]  # round-robin by arrival
     ngmax = 256
-    reqs = [serving.make_request(i, specs[i][0], wl.make_set(*specs[i][1:])) for i in mine]
+    sets = [wl.make_set(*specs[i][1:]) for i in mine]
+    reqs = [serving.make_request(i, specs[i][0], s) for i, s in zip(mine, sets)]
+    tuned = not args.no_tune
+    if tuned:
+        # the autotuner's parameters per class of set, for every request (the
+        # plain path takes the tree parameters among them: s, alpha, beta)
+        from paper_1910_02639_gb300.autotune import Tuner
+        tuner = Tuner(dev, ngmax)
+        tuner.tune(sets)
+        for r, p in zip(reqs, tuner.params_for(sets)):
+            r.params = p
+        del tuner
+        torch.cuda.empty_cache()
+    del sets
     sums, pairs = {}, {}
 
     def grab(tag):
@@ -608,20 +623,24 @@ def run_serving_section(args, dev, dist, rank, ws):
     srv = serving.Server(dev, ngmax=ngmax, slots=args.serving_slots)
     try:
         serving.replay(srv, [serving.make_request(-1, 0.0, wl.make_set("uniform_cube", 50_000, 1, 100.0))])
-        served = serving.replay(srv, reqs, on_result=grab("served"))
+        served = serving.replay(srv, reqs)
         for r in reqs:
             r.arrival = 0.0
         sat = serving.replay(srv, reqs)
+        # the results checked outside the timed replays (the checks run in
+        # the client loop and would delay the submissions)
+        serving.replay(srv, reqs, on_result=grab("served"))
     finally:
         srv.close()
     for r, sp in zip(reqs, (specs[i] for i in mine)):
         r.arrival = sp[0]
     serving.replay_plain([serving.make_request(-1, 0.0, wl.make_set("uniform_cube", 50_000, 1, 100.0))],
                          dev, ngmax)
-    plain = serving.replay_plain(reqs, dev, ngmax, on_result=grab("plain"))
+    plain = serving.replay_plain(reqs, dev, ngmax)
     for r in reqs:
         r.arrival = 0.0
     plain_sat = serving.replay_plain(reqs, dev, ngmax)
+    serving.replay_plain(reqs, dev, ngmax, on_result=grab("plain"))
     total = sum(pairs.values())
     same = all(sums[("served", r.rid)] == sums[("plain", r.rid)] for r in reqs)
     st = serving.latency_stats(served, total)
@@ -639,6 +658,8 @@ def run_serving_section(args, dev, dist, rank, ws):
     out = {"workload": f"poisson_{args.serving_requests}_requests_200_per_s",
            "requests": len(reqs), "particles": int(sum(r.n for r in reqs)), "pairs": total,
            "slots": args.serving_slots, "ngmax": ngmax,
+           "params": "autotuned per class of set (the plain path: s, alpha, beta)" if tuned
+                     else "defaults (s = 16, alpha = beta = 0.5)",
            "served": {k: st[k] for k in ("p50_ms", "p99_ms", "mean_ms", "pairs_per_s")},
            "plain": {k: sp_[k] for k in ("p50_ms", "p99_ms", "mean_ms", "pairs_per_s")},
            "saturated_pairs_per_s": {"served": st_sat, "plain": sp_sat},

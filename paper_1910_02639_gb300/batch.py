@@ -132,12 +132,14 @@ def shard_sets(sizes, world: int):
     return [sorted(o) for o in out]
 
 
-def list_checksum(nb, cnt, ngmax: int, chunk_rows: int = 1 << 20) -> int:
+def list_checksum(nb, cnt, ngmax: int, chunk_rows: int = 1 << 17) -> int:
     """Order-sensitive checksum of the written part of every row (entries
-    past min(count, ngmax) are unspecified and skipped)."""
+    past min(count, ngmax) are unspecified and skipped).  Works in blocks of
+    `chunk_rows` rows (a few hundred MB of temporaries) and reads the result
+    back once."""
     import torch
     n = int(cnt.numel())
-    total = 0
+    total = torch.zeros((), dtype=torch.int64, device=nb.device)
     col = torch.arange(ngmax, device=nb.device, dtype=torch.int64)
     for a in range(0, n, chunk_rows):
         b = min(n, a + chunk_rows)
@@ -145,5 +147,5 @@ def list_checksum(nb, cnt, ngmax: int, chunk_rows: int = 1 << 20) -> int:
         used = col[None, :] < cnt[a:b].to(torch.int64).clamp(max=ngmax)[:, None]
         w = (torch.arange(a, b, device=nb.device, dtype=torch.int64)[:, None] * ngmax + col[None, :])
         w = w % 1000003 + 1
-        total += int(torch.where(used, (rows + 7) * w, torch.zeros_like(rows)).sum().item())
-    return total
+        total += torch.where(used, (rows + 7) * w, torch.zeros_like(rows)).sum()
+    return int(total.item())
