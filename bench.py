@@ -687,10 +687,20 @@ def cpu_baseline(s, cfg, sample):
     t2 = time.perf_counter()
     pairs = int(np.asarray(c, dtype=np.int64).sum())
     secs = (t1 - t0) * q / n + (t2 - t1)
+    # the brute-force definition on the small uniform configuration (32768
+    # particles, every query against every particle), for scale
+    from paper_1910_02639_gb300 import workloads as wl
+    u = wl.uniform_cube(32768, seed=1911)
+    t3 = time.perf_counter()
+    _, cb = oracle.find_brute(u.x, u.y, u.z, u.h, 256)
+    t4 = time.perf_counter()
+    pb = int(np.asarray(cb, dtype=np.int64).sum())
     return {"value": pairs / secs, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"BuildTree on all {n} particles ({t1 - t0:.2f} s, charged pro rata) + "
                       f"FindNeighbors for particles [{q0}, {q0 + q}) ({t2 - t1:.2f} s), {pairs} pairs",
-            "build_s": round(t1 - t0, 3), "find_s": round(t2 - t1, 3)}
+            "build_s": round(t1 - t0, 3), "find_s": round(t2 - t1, 3),
+            "brute_force_uniform_32768": {"pairs_per_s": pb / (t4 - t3), "s": round(t4 - t3, 3),
+                                          "pairs": pb}}
 
 
 def run_reference(args):
