@@ -114,6 +114,31 @@ def test_empty_sets_at_both_ends_and_chunk_boundaries(bt):
         _assert_same(res[i], alone, "set %d (n=%d)" % (i, s.n))
 
 
+def test_thousands_of_tiny_sets(bt, oracle):
+    """2000 sets of 0 to 40 particles (many empty, many one leaf, some split
+    by the warp builder) in one batch: every list, count and density against
+    the oracle's brute force on that set."""
+    rng = np.random.default_rng(77)
+    sets = []
+    for i in range(2000):
+        n = int(rng.integers(0, 41))
+        sets.append(wl.uniform_cube(n, seed=1000 + i, target=8) if n else
+                    wl._pack(np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0)))
+    params = [dict(bucket_size=int(rng.choice([1, 4, 16]))) for _ in sets]
+    tree, off, res = run_batched(bt, sets, params=params, ngmax=64)
+    tree.free()
+    worst = 0.0
+    for i, s in enumerate(sets):
+        if s.n == 0:
+            continue
+        ref_nb, ref_cnt = oracle.find_brute(s.x, s.y, s.z, s.h, 64)
+        assert np.array_equal(res[i]["cnt"], ref_cnt), f"set {i}: counts"
+        assert np.array_equal(res[i]["nb"], ref_nb), f"set {i}: lists"
+        ref_rho = oracle.OracleTree(s.x, s.y, s.z, bucket_size=16).density(s.h, s.m)
+        worst = max(worst, float(np.max(np.abs(res[i]["rho"] - ref_rho) / ref_rho)))
+    assert worst < 1e-5
+
+
 def test_batched_trees_match_the_oracle_per_set(bt, oracle):
     sets = _mixed_sets()
     params = [dict(bucket_size=(16, 5, 1, 8)[i % 4], beta=(0.5, 0.0, 1.0)[i % 3],
