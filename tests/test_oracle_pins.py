@@ -121,6 +121,41 @@ def test_beta_one_never_halves_and_beta_zero_always_halves(oracle):
     assert np.all(b[b > 0] == 2)  # every internal node collapses to an octree split
 
 
+def _checkerboard_cells(drop=0):
+    """One particle at the centre of each sub-cell (x+y+z even) of a 4x4x4
+    grid: 32 occupied, 32 empty, and 0 and 3 occur in every dimension, so the
+    bounding box maps the centres onto exactly these sub-cells (Eq. 2).
+    `drop` removes that many occupied cells that do not set the box."""
+    c = [(i, j, k) for k in range(4) for j in range(4) for i in range(4) if (i + j + k) % 2 == 0]
+    keep = [t for t in c if 0 in t or 3 in t]
+    inner = [t for t in c if t not in keep]
+    c = keep + inner[:len(inner) - drop] if drop else c
+    p = np.array(c, np.float32) + np.float32(0.5)
+    return p[:, 0].copy(), p[:, 1].copy(), p[:, 2].copy()
+
+
+def test_ratio_tie_accepts(oracle):
+    # Eq. 4 at equality.  s = 1, alpha = 0.5: a sub-cell is underfull iff it is
+    # empty.  32 particles: b0 = 4 (27 < 32 <= 64), 32 of the 64 sub-cells
+    # empty, u = 32 = beta * b^3 exactly: r is not larger than beta, so b = 4
+    # is kept (Sec. 3.1, step 3: halve only while r exceeds beta).
+    x, y, z = _checkerboard_cells()
+    assert x.shape[0] == 32 and oracle.branching_factor(32, 1) == 4
+    e = oracle.OracleTree(x, y, z, bucket_size=1, alpha=0.5, beta=0.5).export()
+    assert e["b"][0] == 4
+    # every occupied sub-cell holds one particle: a leaf, no deeper node
+    assert np.count_nonzero(e["b"]) == 1
+
+
+def test_ratio_one_past_tie_halves(oracle):
+    # the same grid with two inner occupied cells removed: 30 particles,
+    # b0 = 4 still (27 < 30), u = 34 > 32: halve to b = 2.
+    x, y, z = _checkerboard_cells(drop=2)
+    assert x.shape[0] == 30 and oracle.branching_factor(30, 1) == 4
+    e = oracle.OracleTree(x, y, z, bucket_size=1, alpha=0.5, beta=0.5).export()
+    assert e["b"][0] == 2
+
+
 # --------------------------------------------------------------- tree invariants
 def _check_tree_invariants(e, n, s, k=3):
     leaf = e["b"] == 0
