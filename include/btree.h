@@ -280,7 +280,10 @@ int btree_find_neighbors_density(const btree_t *t, const float *m, int ngmax,
  *    process exits.
  *  - The first call on a device looks up the array's device address (once
  *    per device, with that device current); make that first call before any
- *    CUDA stream capture.
+ *    CUDA stream capture.  The device current at the call must be the one
+ *    the tree was built on (else BT_ERR_ARG).  The address belongs to that
+ *    device's primary context: after cudaDeviceReset it is stale, so do not
+ *    use this entry point again in a process that reset the device.
  *  - All calls share the one array: calls whose GPU work overlaps in time
  *    (different streams, or different threads) race on it and may return
  *    wrong densities.  Serialise them (same stream, or events).

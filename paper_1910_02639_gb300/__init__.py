@@ -22,7 +22,7 @@ __all__ = [
     "btree_find_neighbors_density", "btree_find_neighbors_density_noalloc",
     "btree_noalloc_max_particles", "sph_density", "btree_status", "btree_get_info",
     "btree_export", "btree_free", "btree_strerror", "btree_version", "btree_kernel_launches",
-    "btree_arith_rates",
+    "btree_arith_rates", "Allocator", "torch_allocator",
     "library_path",
     "BT_OK", "BT_WARN_NGMAX", "BT_WARN_OVERSIZED_LEAF",
 ]
@@ -147,6 +147,48 @@ def _check(status: int, what: str) -> int:
     return status
 
 
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _CAllocator(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("alloc", _ALLOC_FN), ("free", _FREE_FN)]
+
+
+class Allocator:
+    """A bt_allocator (include/btree.h) from two Python callables:
+    ``alloc(nbytes, stream) -> device address`` (an int; 0 or None when out
+    of memory) and ``free(address, stream)``; ``stream`` is the cudaStream_t
+    as an int.  A tree built with it takes every internal buffer from it and
+    returns them through it when freed.  The callbacks must not raise."""
+
+    def __init__(self, alloc, free):
+        def _a(ctx, nbytes, stream):
+            try:
+                p = alloc(int(nbytes), int(stream or 0))
+            except Exception:
+                p = 0
+            return int(p) if p else None
+
+        def _f(ctx, ptr, stream):
+            try:
+                free(int(ptr or 0), int(stream or 0))
+            except Exception:
+                pass
+
+        self._a, self._f = _ALLOC_FN(_a), _FREE_FN(_f)  # kept alive with the allocator
+        self.c = _CAllocator(None, self._a, self._f)
+
+
+def torch_allocator(device=None) -> Allocator:
+    """PyTorch's caching allocator behind a tree's buffers (stream-ordered
+    reuse on the stream the library passes)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    return Allocator(lambda n, st: torch.cuda.caching_allocator_alloc(n, dev, st),
+                     lambda p, st: torch.cuda.caching_allocator_delete(p))
+
+
 class Tree:
     """Owns one btree_t.  Keeps the last build status in ``status``."""
 
@@ -154,6 +196,7 @@ class Tree:
         self._ptr = ctypes.c_void_p(None)
         self.status = BT_OK
         self.n = 0
+        self._allocator = None  # keeps an Allocator's callbacks alive until free()
 
     @property
     def handle(self):
@@ -163,6 +206,7 @@ class Tree:
         if self._ptr and self._ptr.value:
             _load().btree_free(self._ptr)
         self._ptr = ctypes.c_void_p(None)
+        self._allocator = None
 
     def __del__(self):
         try:
@@ -175,14 +219,18 @@ class Tree:
 
 
 def btree_build(x, y, z, h, bucket_size: int = 16, alpha: float = 0.5, beta: float = 0.5,
-                stream=None, tree: Tree | None = None) -> Tree:
-    """BuildTree (Algorithm 1).  Rebuilds `tree` in place when given."""
+                stream=None, tree: Tree | None = None, allocator: Allocator | None = None) -> Tree:
+    """BuildTree (Algorithm 1).  Rebuilds `tree` in place when given.  With
+    `allocator` the tree's buffers come from it (else cudaMallocAsync)."""
     import torch
     lib = _load()
     n = int(x.numel())
     ptrs = [_dptr(a, torch.float32, nm, n) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (h, "h"))]
     t = tree if tree is not None else Tree()
-    st = lib.btree_build(*ptrs, n, int(bucket_size), float(alpha), float(beta), None,
+    if allocator is not None:
+        t._allocator = allocator
+    st = lib.btree_build(*ptrs, n, int(bucket_size), float(alpha), float(beta),
+                         ctypes.byref(allocator.c) if allocator is not None else None,
                          ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(t._ptr))
     _check(st, "btree_build")
     t.status = st

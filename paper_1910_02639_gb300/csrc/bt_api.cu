@@ -624,7 +624,10 @@ static btree *prepare_handle(btree_t **out, const bt_allocator *alloc, void *str
         *out = t;
     }
     if (alloc) {
-        if (!fresh && !t->has_al) free_all(t);  // buffers came from another allocator
+        // buffers from another allocator (or the default) go back to it first
+        const bool same = t->has_al && t->al.ctx == alloc->ctx && t->al.alloc == alloc->alloc &&
+                          t->al.free == alloc->free;
+        if (!fresh && !same) free_all(t);
         t->al = *alloc;
         t->has_al = true;
     } else if (t->has_al) {
@@ -872,6 +875,10 @@ int btree_find_neighbors_density_noalloc(const btree_t *t, const float *m, int n
     if (!t || ngmax < 1 || (t->n > 0 && (!neighbors || !counts || !m || !rho))) return BT_ERR_ARG;
     if (t->n > noalloc_max_particles()) return BT_ERR_CAPACITY;
     if (t->n == 0) return BT_OK;
+    // the scratch address is looked up for the current device: it must be
+    // the tree's
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != t->device) return BT_ERR_ARG;
     return to_status(launch_find_density_noalloc(view(t), t->ngroups, t->ngroups_c, ngmax, neighbors, counts, m,
                                                  rho, t->sms, static_cast<cudaStream_t>(stream)));
 }
