@@ -655,6 +655,7 @@ def run_serving_section(args, dev, dist, rank, ws):
         dist.all_reduce(t)
         st["pairs_per_s"], sp_["pairs_per_s"], st_sat, sp_sat = (float(v) for v in t[:4])
         same = t[4].item() == 0.0
+    sweep = run_serving_sweep(args, dev, reqs, pairs, ngmax) if not args.no_serving_sweep else None
     out = {"workload": f"poisson_{args.serving_requests}_requests_200_per_s",
            "requests": len(reqs), "particles": int(sum(r.n for r in reqs)), "pairs": total,
            "slots": args.serving_slots, "ngmax": ngmax,
@@ -666,6 +667,57 @@ def run_serving_section(args, dev, dist, rank, ws):
            "ranks": ws,
            "mean_batch_size": float(np.mean([r.batch_size for r in served])),
            "identical_to_plain": bool(same)}
+    if sweep is not None:
+        out["sweep"] = sweep
+    return out
+
+
+def run_serving_sweep(args, dev, pool, pool_pairs, ngmax):
+    """Arrival-rate sweep: for each rate, args.serving_sweep_requests Poisson
+    arrivals (seeded) whose sets are drawn in turn from the request pool of
+    the 200-request stream (same pinned host arrays, same per-class
+    parameters); served by the continuous-batching loop and by the plain path
+    under the same arrivals.  Reports latency percentiles, throughput and how
+    many requests a batch held."""
+    import numpy as np
+    from paper_1910_02639_gb300 import serving
+    out = []
+    nreq = args.serving_sweep_requests
+    for k, rate in enumerate(args.serving_rates):
+        rng = np.random.Generator(np.random.PCG64(1917 + k))
+        t = np.cumsum(rng.exponential(1.0 / rate, nreq))
+        reqs = []
+        for i in range(nreq):
+            src = pool[i % len(pool)]
+            r = serving.Request(i, float(t[i]), src.x, src.y, src.z, src.h, src.m, dict(src.params))
+            reqs.append(r)
+        total = sum(pool_pairs[pool[i % len(pool)].rid] for i in range(nreq))
+        srv = serving.Server(dev, ngmax=ngmax, slots=args.serving_slots)
+        try:
+            served = serving.replay(srv, reqs)
+            tl = list(srv.timeline)
+        finally:
+            srv.close()
+        plain = serving.replay_plain(reqs, dev, ngmax)
+        st = serving.latency_stats(served, total)
+        sp_ = serving.latency_stats(plain, total)
+        # device time covered by two or more slots at once
+        ev = sorted([(a, 1) for _, _, a, _, _ in tl] + [(b, -1) for _, _, _, b, _ in tl])
+        depth, last, multi, busy = 0, None, 0.0, 0.0
+        for x, d in ev:
+            if last is not None and depth > 0:
+                busy += x - last
+                if depth > 1:
+                    multi += x - last
+            depth += d
+            last = x
+        out.append({"rate_per_s": rate, "requests": nreq, "pairs": total,
+                    "served": {kk: st[kk] for kk in ("p50_ms", "p99_ms", "mean_ms", "pairs_per_s")},
+                    "plain": {kk: sp_[kk] for kk in ("p50_ms", "p99_ms", "mean_ms", "pairs_per_s")},
+                    "mean_batch_size": float(np.mean([r.batch_size for r in served])),
+                    "max_batch_size": int(max(r.batch_size for r in served)),
+                    "batches": len(tl),
+                    "device_overlap_frac": multi / busy if busy > 0 else 0.0})
     return out
 
 
@@ -763,6 +815,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=200)
     ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--no-serving-sweep", action="store_true")
+    ap.add_argument("--serving-sweep-requests", type=int, default=2000)
+    ap.add_argument("--serving-rates", type=float, nargs="+", default=[200.0, 1000.0, 4000.0])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -11,8 +11,11 @@ admitted as slots and memory free up, and batches on different slots overlap
 on the device.
 
 Results stay in device memory (views of the batch's output buffers) until the
-client releases them; the batch's memory returns to the budget when all of
-its results are released.  A request the library rejects (non-finite
+client releases them; the batch's inputs and outputs return to the budget
+when all of its results are released.  Each slot keeps its tree between
+batches; the tree's bound (tree_bytes) stays charged to the slot, and a batch
+is charged only for the growth of its slot's tree.  Every batch's span on the
+device (CUDA events on its slot's stream) is kept in Server.timeline.  A request the library rejects (non-finite
 coordinates or smoothing lengths) fails alone: its batch is re-run request by
 request and only it returns an error result.  Each request's lists, counts
 and densities are bit-identical to those of the same set run alone: sets in a
@@ -32,11 +35,22 @@ import numpy as np
 from . import BtreeError, btree_build, btree_build_batched, btree_find_neighbors_density
 
 
+def io_bytes(n: int, ngmax: int) -> int:
+    """Device bytes of one request's inputs (x, y, z, h, m) and outputs (rows,
+    counts, densities): held until its result is released."""
+    return int(n) * (5 * 4 + 4 * ngmax + 4 + 4) + (1 << 20)
+
+
+def tree_bytes(n: int) -> int:
+    """A generous bound on a tree's buffers for n particles (sorted copy,
+    permutation, working buffers, nodes, sub-cells, work units).  A slot keeps
+    its tree between batches, so this stays charged to the slot."""
+    return int(n) * 96 + (1 << 20)
+
+
 def request_bytes(n: int, ngmax: int) -> int:
-    """Device bytes one request holds while in flight: inputs (x, y, z, h, m),
-    outputs (rows, counts, densities) and the tree (sorted copy, permutation,
-    working buffers, nodes and sub-cells; a generous per-particle bound)."""
-    return int(n) * (5 * 4 + 4 * ngmax + 4 + 4 + 96) + (1 << 20)
+    """Device bytes one request needs on a slot that holds no tree yet."""
+    return io_bytes(n, ngmax) + tree_bytes(n)
 
 
 @dataclass
@@ -69,6 +83,7 @@ class Result:
     batch_size: int
     _batch_ref: object = None
     error: str | None = None       # set when the request failed (then nb/cnt/rho are None)
+    slot: int = -1                 # the worker slot that ran it
 
     @property
     def latency(self) -> float:
@@ -125,6 +140,11 @@ class Server:
         self._work = [queue.Queue() for _ in range(self.slots)]
         self._streams = [torch.cuda.Stream(self.device) for _ in range(self.slots)]
         self._trees = [None] * self.slots
+        self._slot_tree = [0] * self.slots  # bytes charged for each slot's kept tree
+        # per batch on the device: (batch, slot, start_ms, end_ms, requests),
+        # from CUDA events on the slot's stream, relative to start_clock()
+        self.timeline: list[tuple] = []
+        self._ref = None
         self._t0 = None
         self._nbatch = 0
         self._stop = False
@@ -136,7 +156,10 @@ class Server:
 
     # ------------------------------------------------------------ clock
     def start_clock(self, t0: float | None = None):
+        import torch
         self._t0 = time.perf_counter() if t0 is None else t0
+        self._ref = torch.cuda.Event(enable_timing=True)
+        self._ref.record(torch.cuda.current_stream(self.device))
 
     def now(self) -> float:
         return time.perf_counter() - self._t0
@@ -183,26 +206,51 @@ class Server:
 
     def _admit_locked(self):
         """FIFO admission: while a slot is idle, take the longest prefix of the
-        waiting queue that fits the free budget and the batch limit."""
+        waiting queue that fits the free budget and the batch limit.  A batch
+        costs its inputs and outputs plus whatever its tree needs beyond the
+        tree the slot already holds (that stays charged to the slot)."""
         while self._idle and self._waiting:
-            take, nbytes, npart = [], 0, 0
+            slot = self._idle[0]
+            have = self._slot_tree[slot]
+            take, nbytes, npart, grow = [], 0, 0, 0
             for r in self._waiting:
-                b = request_bytes(r.n, self.ngmax)
-                if nbytes + b > self._free_bytes:
+                b = io_bytes(r.n, self.ngmax)
+                g = max(0, tree_bytes(npart + r.n) - have)
+                if nbytes + b + g > self._free_bytes:
                     break
                 if take and npart + r.n > self.max_batch_particles:
                     break
                 take.append(r)
                 nbytes += b
                 npart += r.n
+                grow = g
             if not take:
-                return  # the head waits for memory
+                # the head waits for memory -- unless trees kept by other idle
+                # slots hold it: free those and try again
+                if self._reclaim_locked(keep=slot):
+                    continue
+                return
             del self._waiting[:len(take)]
-            self._free_bytes -= nbytes
-            slot = self._idle.pop(0)
+            self._free_bytes -= nbytes + grow
+            self._slot_tree[slot] += grow
+            self._idle.pop(0)
             self._nbatch += 1
             t_adm = self.now() if self._t0 is not None else 0.0
             self._work[slot].put((self._nbatch, take, nbytes, t_adm))
+
+    def _reclaim_locked(self, keep: int) -> bool:
+        """Free the trees of idle slots other than `keep` (no work of theirs
+        is in flight); True when that returned any bytes."""
+        got = 0
+        for k in self._idle:
+            if k != keep and self._slot_tree[k] > 0:
+                if self._trees[k] is not None:
+                    self._trees[k].free()
+                    self._trees[k] = None
+                got += self._slot_tree[k]
+                self._slot_tree[k] = 0
+        self._free_bytes += got
+        return got > 0
 
     # ------------------------------------------------------------ workers
     def _worker(self, slot):
@@ -222,7 +270,7 @@ class Server:
                 # that only the bad ones fail
                 held = nbytes
                 for r in reqs:
-                    one = request_bytes(r.n, self.ngmax)
+                    one = io_bytes(r.n, self.ngmax)
                     try:
                         self._run_batch(slot, st, bid, [r], one, t_adm)
                         held -= one  # now owned by that result's buffers
@@ -247,7 +295,10 @@ class Server:
         off[1:] = np.cumsum(sizes)
         n = int(off[-1])
         n1 = max(n, 1)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(st):
+            ev0.record(st)
             dev = self.device
             x, y, z, h, m = (torch.empty(n1, dtype=torch.float32, device=dev) for _ in range(5))
             for r, a, b in zip(reqs, off[:-1], off[1:]):
@@ -262,14 +313,18 @@ class Server:
             self._trees[slot] = btree_build_batched(x[:n], y[:n], z[:n], h[:n], off, params,
                                                     stream=st, tree=self._trees[slot])
             btree_find_neighbors_density(self._trees[slot], m[:n], g, nb, cnt, rho, stream=st)
+            ev1.record(st)
         st.synchronize()
         t_done = self.now()
+        if self._ref is not None:
+            self.timeline.append((bid, slot, self._ref.elapsed_time(ev0), self._ref.elapsed_time(ev1),
+                                  len(reqs)))
         batch = _Batch(self, reqs, nbytes)
         batch.bufs = (x, y, z, h, m, nb, cnt, rho)
         for r, a, b in zip(reqs, off[:-1], off[1:]):
             a, b = int(a), int(b)
             self._done.put(Result(r.rid, r.n, nb[a * g:b * g], cnt[a:b], rho[a:b], r.arrival,
-                                  t_adm, t_done, bid, len(reqs), batch))
+                                  t_adm, t_done, bid, len(reqs), batch, slot=slot))
 
 
 # ---------------------------------------------------------------- replay

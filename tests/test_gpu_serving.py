@@ -107,3 +107,36 @@ def test_a_bad_request_fails_alone(srv_mod):
         a, b = served[r.rid], alone[r.rid]
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
         assert np.array_equal(a[2].view(np.int32), b[2].view(np.int32))
+
+
+def test_batches_on_different_slots_overlap_on_the_device(srv_mod):
+    # continuous batching, not a queue: with requests arriving while others
+    # run, batches of different slots are on the GPU at the same time (CUDA
+    # event spans on the slots' streams)
+    reqs = _requests(srv_mod, 24, seed=705, nmin=50_000, nmax=400_000, spread=0.02)
+    srv = srv_mod.Server(ngmax=NGMAX, slots=3, max_batch_particles=500_000)
+    try:
+        out = srv_mod.replay(srv, reqs)
+        tl = list(srv.timeline)
+    finally:
+        srv.close()
+    assert len(out) == len(reqs) and not srv.errors
+    assert len({slot for _, slot, _, _, _ in tl}) >= 2
+    overlaps = [(a[0], b[0]) for i, a in enumerate(tl) for b in tl[i + 1:]
+                if a[1] != b[1] and a[2] < b[3] and b[2] < a[3]]
+    assert overlaps, f"no two batches of different slots overlapped on the device: {tl}"
+
+
+def test_slot_trees_stay_charged_to_the_budget(srv_mod):
+    # a slot keeps its tree after its batch: the budget accounts for it until
+    # the tree is freed, and in-flight plus kept bytes never exceed the budget
+    reqs = _requests(srv_mod, 10, seed=706, nmin=10_000, nmax=40_000)
+    srv = srv_mod.Server(ngmax=NGMAX, slots=2)
+    seen = []
+    try:
+        srv_mod.replay(srv, reqs, on_result=lambda r: seen.append(srv.budget - srv._free_bytes))
+        kept = sum(srv._slot_tree)
+        assert kept > 0 and srv.budget - srv._free_bytes == kept
+    finally:
+        srv.close()
+    assert max(seen) <= srv.budget
