@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <mutex>
 #include <new>
 
@@ -93,6 +94,19 @@ struct btree {
     cudaStream_t gs[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t gexec = nullptr;
     GraphKey gkey{};
+    // asynchronous rebuilds: the build alone as a graph (its own executable),
+    // launched without waiting once an earlier build of the same size has set
+    // the buffer capacities.  `pending`: its host-side finish (counters, info)
+    // is still to be read; ev_staged: its per-set records were read;
+    // ev_built: it finished (counters in mapped host memory).
+    cudaGraphExec_t gexec_b = nullptr;
+    GraphKey gkey_b{};
+    bool pending = false;
+    cudaEvent_t ev_staged = nullptr, ev_built = nullptr;
+    int64_t async_n = -1;
+    int async_nsets = -1;
+    SetRec *async_rec = nullptr;  // host copy of the records of the last synchronous build
+    int cap_async_rec = 0;
 };
 
 namespace {
@@ -163,6 +177,7 @@ void free_all(btree *t)
     t->big = nullptr; t->small = nullptr; t->ctr = nullptr; t->smass = nullptr;
     t->cap_n = 0; t->cap_nodes = t->cap_slots = t->cap_groups = t->cap_small = t->cap_big = 0;
     t->cap_hist = 0; t->cap_smass = 0;
+    t->async_n = -1;  // the capacities are gone: the next build is synchronous
 }
 
 TreeDev view(const btree *t)
@@ -336,6 +351,7 @@ void launch_build_head(btree *t, const TreeDev &T, const LevelBufs &L, cudaStrea
     launch_init_counters(t->ctr, t->nsets, st);
     launch_init_sets(T, t->h_rec_dev, t->set_start, t->set_s, t->set_na, t->set_beta, t->set_gmax,
                      t->set_chunk0, st);
+    if (capture && t->ev_staged) record_event(t->ev_staged, st, true);
     record_event(t->ev0, st, capture);
     launch_bbox(T, L.in.x, L.in.y, L.in.z, L.in.h, t->root_chunks, t->sms, st);
     launch_roots(T, L, t->root_chunks, t->sms, st);
@@ -475,6 +491,11 @@ cudaError_t capture_step(btree *t, const GraphKey &K, cudaGraph_t *out)
     }
     launch_small(T, L, t->cap_small, t->sms, s0);
     record_event(t->ev1, s0, true);
+    if (!K.nbrs) {
+        // the build alone: counters to mapped host memory, then its event
+        launch_readback(t->ctr, t->walk, t->rb_dev, s0);
+        if (t->ev_built) record_event(t->ev_built, s0, true);
+    }
     if (K.nbrs) chk(launch_find(T, -1, -1, K.ngmax, K.nbrs, K.counts, K.m, K.smass, K.rho, t->sms, s0));
     cudaGraph_t g = nullptr;
     chk(cudaStreamEndCapture(s0, &g));
@@ -493,7 +514,78 @@ uint64_t graph_launches(const Counters &c, bool find, bool dens)
     // head: init_counters, init_sets, bbox, root_sets, copy_leaf_roots, level_go;
     // per level: begin, setup, scan, zero, finish, 3 scans, emit, scatter, level_go;
     // per ratio pass: hist, count, decide, zero, ratio_end; then small and find
-    return 6 + 11 * (uint64_t)c.level + 5 * (uint64_t)c.ratio_total + 1 + (find ? 1 + (dens ? 1 : 0) : 0);
+    // (find: the two work-unit lists and the pass over the units split by them)
+    return 6 + 11 * (uint64_t)c.level + 5 * (uint64_t)c.ratio_total + 1 + (find ? 3 + (dens ? 1 : 0) : 0);
+}
+
+// Launches the captured step (captured again when a pointer or size
+// changed); the build-only graph and the build + find graph are kept apart.
+cudaError_t launch_step_graph(btree *t, const GraphKey &K, cudaStream_t user)
+{
+    const bool build_only = K.nbrs == nullptr;
+    cudaGraphExec_t &gx = build_only ? t->gexec_b : t->gexec;
+    GraphKey &gk = build_only ? t->gkey_b : t->gkey;
+    if (!gx || std::memcmp(&K, &gk, sizeof(GraphKey)) != 0) {
+        cudaGraph_t g = nullptr;
+        g_capturing = true;
+        cudaError_t e = capture_step(t, K, &g);
+        g_capturing = false;
+        if (e != cudaSuccess) return e;
+        bool updated = false;
+        if (gx) {
+            cudaGraphExecUpdateResultInfo info;
+            updated = cudaGraphExecUpdate(gx, g, &info) == cudaSuccess;
+            if (!updated) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(gx);
+                gx = nullptr;
+            }
+        }
+        if (!updated) e = cudaGraphInstantiate(&gx, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            gx = nullptr;
+            return e;
+        }
+        std::memcpy(&gk, &K, sizeof(GraphKey));
+    }
+    return cudaGraphLaunch(gx, user);
+}
+
+// The host-side end of an asynchronous build: wait for it, read its
+// counters, account its launches.  A build that ran out of capacity (or saw
+// non-finite input) reports it here, and the next build runs synchronously
+// with retries.
+int finish_pending(btree *t)
+{
+    if (!t->pending) return BT_OK;
+    t->pending = false;
+    cudaError_t e = cudaEventSynchronize(t->ev_built);
+    if (e != cudaSuccess) return to_status(e);
+    note_launch((int)(graph_launches(*t->hctr, false, false) + 1));
+    const int rc = finish_build(t, t->st);
+    if (rc == kRetry || rc < 0) t->async_n = -1;
+    return rc == kRetry ? BT_ERR_CAPACITY : rc;
+}
+
+// The build alone, as one graph launch on `user`, without waiting for it.
+int run_graph_build_async(btree *t, const float *x, const float *y, const float *z, const float *h,
+                          cudaStream_t user)
+{
+    for (int k = 0; k < 3; k++)
+        if (!t->gs[k] && cudaStreamCreateWithFlags(&t->gs[k], cudaStreamNonBlocking) != cudaSuccess)
+            return BT_ERR_CUDA;
+    GraphKey K;
+    std::memset(&K, 0, sizeof(K));
+    K.T = view(t);
+    K.L = lview(t, x, y, z, h);
+    K.rec = t->h_rec_dev;
+    K.sms = t->sms;
+    K.root_chunks = t->root_chunks;
+    cudaError_t e = launch_step_graph(t, K, user);
+    if (e != cudaSuccess) return to_status(e);
+    t->pending = true;
+    return BT_OK;
 }
 
 int run_graph_step(btree *t, const float *x, const float *y, const float *z, const float *h,
@@ -516,33 +608,9 @@ int run_graph_step(btree *t, const float *x, const float *y, const float *z, con
     K.ngmax = ngmax;
     K.sms = t->sms;
     K.root_chunks = t->root_chunks;
-    if (!t->gexec || std::memcmp(&K, &t->gkey, sizeof(GraphKey)) != 0) {
-        cudaGraph_t g = nullptr;
-        g_capturing = true;
-        cudaError_t e = capture_step(t, K, &g);
-        g_capturing = false;
-        if (e != cudaSuccess) return to_status(e);
-        bool updated = false;
-        if (t->gexec) {
-            cudaGraphExecUpdateResultInfo info;
-            updated = cudaGraphExecUpdate(t->gexec, g, &info) == cudaSuccess;
-            if (!updated) {
-                cudaGetLastError();
-                cudaGraphExecDestroy(t->gexec);
-                t->gexec = nullptr;
-            }
-        }
-        if (!updated) e = cudaGraphInstantiate(&t->gexec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-            t->gexec = nullptr;
-            return to_status(e);
-        }
-        std::memcpy(&t->gkey, &K, sizeof(GraphKey));
-    }
     // the graph runs on the private stream s0's ordering inside; it is
     // launched on the caller's stream
-    cudaError_t e = cudaGraphLaunch(t->gexec, user);
+    cudaError_t e = launch_step_graph(t, K, user);
     if (e != cudaSuccess) return to_status(e);
     int rc = read_counters(t, user);
     if (rc != BT_OK) return rc;
@@ -562,6 +630,14 @@ static int build_core(btree *t, const float *x, const float *y, const float *z, 
                       cudaStream_t user = nullptr)
 {
     int rc = BT_OK;
+    // steady state: the sizes of the last synchronous build, whose capacities
+    // held -- the build runs as one graph launch and the call returns at once
+    if (!graph && t->n > 0 && t->async_n == t->n && t->async_nsets == t->nsets && t->ev_built &&
+        t->async_rec && std::memcmp(t->async_rec, t->h_rec, sizeof(SetRec) * (size_t)t->nsets) == 0) {
+        rc = run_graph_build_async(t, x, y, z, h, t->st);
+        if (rc == BT_OK) return BT_OK;
+        cudaGetLastError();  // could not launch it: build synchronously
+    }
     for (int attempt = 0; attempt < 6; attempt++) {
         rc = ensure_particle_caps(t, t->n);
         if (rc == BT_OK) rc = ensure_hist(t);
@@ -586,6 +662,20 @@ static int build_core(btree *t, const float *x, const float *y, const float *z, 
         t->cap_slots = (int)cs;
         t->cap_small = (int)cm;
         rc = BT_ERR_CAPACITY;
+    }
+    if (rc >= 0 && !graph) {
+        // the same sets and parameters (new positions allowed) may now be
+        // rebuilt asynchronously in these buffers
+        if (t->cap_async_rec < t->nsets) {
+            std::free(t->async_rec);
+            t->async_rec = static_cast<SetRec *>(std::malloc(sizeof(SetRec) * (size_t)t->nsets));
+            t->cap_async_rec = t->async_rec ? t->nsets : 0;
+        }
+        if (t->async_rec) {
+            std::memcpy(t->async_rec, t->h_rec, sizeof(SetRec) * (size_t)t->nsets);
+            t->async_n = t->n;
+            t->async_nsets = t->nsets;
+        }
     }
     return rc;
 }
@@ -621,7 +711,16 @@ static btree *prepare_handle(btree_t **out, const bt_allocator *alloc, void *str
             return nullptr;
         }
         t->hctr = &t->rb->c;
+        if (cudaEventCreateWithFlags(&t->ev_staged, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&t->ev_built, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            t->ev_staged = t->ev_built = nullptr;  // no asynchronous rebuilds then
+        }
         *out = t;
+    } else if (t->pending) {
+        // the previous asynchronous build must be finished (its records are
+        // restaged and its buffers may be reallocated below)
+        finish_pending(t);
     }
     if (alloc) {
         // buffers from another allocator (or the default) go back to it first
@@ -845,8 +944,9 @@ int btree_find_neighbors(const btree_t *t, int ngmax, int32_t *neighbors, int32_
     if (!t || ngmax < 1 || (t->n > 0 && (!neighbors || !counts))) return BT_ERR_ARG;
     if (t->n == 0) return BT_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    return to_status(launch_find(view(t), t->ngroups, t->ngroups_c, ngmax, neighbors, counts, nullptr, nullptr,
-                                 nullptr, t->sms, st));
+    const bool dc = t->pending;  // counts not on the host yet: read on the device
+    return to_status(launch_find(view(t), dc ? -1 : t->ngroups, dc ? -1 : t->ngroups_c, ngmax, neighbors, counts,
+                                 nullptr, nullptr, nullptr, t->sms, st));
 }
 
 int btree_find_neighbors_density(const btree_t *tc, const float *m, int ngmax, int32_t *neighbors,
@@ -864,8 +964,9 @@ int btree_find_neighbors_density(const btree_t *tc, const float *m, int ngmax, i
         if (!ok) return BT_ERR_OOM;
         t->cap_smass = t->n;
     }
-    return to_status(launch_find(view(t), t->ngroups, t->ngroups_c, ngmax, neighbors, counts, m, t->smass, rho,
-                                 t->sms, st));
+    const bool dc = t->pending;  // counts not on the host yet: read on the device
+    return to_status(launch_find(view(t), dc ? -1 : t->ngroups, dc ? -1 : t->ngroups_c, ngmax, neighbors, counts,
+                                 m, t->smass, rho, t->sms, st));
 }
 
 int btree_find_neighbors_density_noalloc(const btree_t *t, const float *m, int ngmax,
@@ -879,8 +980,10 @@ int btree_find_neighbors_density_noalloc(const btree_t *t, const float *m, int n
     // the tree's
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != t->device) return BT_ERR_ARG;
-    return to_status(launch_find_density_noalloc(view(t), t->ngroups, t->ngroups_c, ngmax, neighbors, counts, m,
-                                                 rho, t->sms, static_cast<cudaStream_t>(stream)));
+    const bool dc = t->pending;  // counts not on the host yet: read on the device
+    return to_status(launch_find_density_noalloc(view(t), dc ? -1 : t->ngroups, dc ? -1 : t->ngroups_c, ngmax,
+                                                 neighbors, counts, m, rho, t->sms,
+                                                 static_cast<cudaStream_t>(stream)));
 }
 
 int64_t btree_noalloc_max_particles(void) { return noalloc_max_particles(); }
@@ -890,6 +993,8 @@ int btree_pack_rows(const btree_t *tc, const int32_t *rows, const int32_t *count
 {
     btree *t = const_cast<btree *>(tc);
     if (!t || ngmax < 1 || !offsets || capacity < 0 || (t->n > 0 && (!rows || !counts))) return BT_ERR_ARG;
+    const int prc = finish_pending(t);
+    if (prc < 0) return prc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t n = t->n;
     if (n == 0) {
@@ -926,6 +1031,8 @@ int btree_find_neighbors_csr(const btree_t *tc, int flags, const float *m, float
     if (!t || !offsets || (m == nullptr) != (rho == nullptr) || capacity < 0) return BT_ERR_ARG;
     if ((flags & ~BT_FIND_HALF) || ((flags & BT_FIND_HALF) && m)) return BT_ERR_ARG;
     const int half = (flags & BT_FIND_HALF) ? 1 : 0;
+    const int prc = finish_pending(t);
+    if (prc < 0) return prc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t n = t->n;
     if (n == 0) {
@@ -977,6 +1084,8 @@ int sph_density(const btree_t *t, const float *m, const int32_t *neighbors, cons
 int btree_status(btree_t *t, void *stream, int *out)
 {
     if (!t || !out) return BT_ERR_ARG;
+    const int prc = finish_pending(t);
+    if (prc == BT_ERR_CUDA) return prc;
     unsigned st = 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (t->ctr) {
@@ -996,9 +1105,12 @@ int btree_status(btree_t *t, void *stream, int *out)
     return BT_OK;
 }
 
-int btree_get_info(const btree_t *t, bt_info *info)
+int btree_get_info(const btree_t *tc, bt_info *info)
 {
-    if (!t || !info) return BT_ERR_ARG;
+    if (!tc || !info) return BT_ERR_ARG;
+    btree *t = const_cast<btree *>(tc);
+    const int rc = finish_pending(t);
+    if (rc < 0) return rc;
     *info = t->info;
     return BT_OK;
 }
@@ -1008,6 +1120,8 @@ int btree_export(const btree_t *t, void *stream, double *node_lo, double *node_h
                  int32_t *slot_start, int32_t *slot_count, int32_t *slot_child, int32_t *order)
 {
     if (!t) return BT_ERR_ARG;
+    const int prc = finish_pending(const_cast<btree *>(t));
+    if (prc < 0) return prc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t nn = t->info.num_nodes, ns = t->info.num_slots, n = t->n;
     NodeGeom *g = nullptr;
@@ -1066,7 +1180,12 @@ int btree_export(const btree_t *t, void *stream, double *node_lo, double *node_h
 void btree_free(btree_t *t)
 {
     if (!t) return;
+    if (t->pending) cudaEventSynchronize(t->ev_built);
     if (t->gexec) cudaGraphExecDestroy(t->gexec);
+    if (t->gexec_b) cudaGraphExecDestroy(t->gexec_b);
+    if (t->ev_staged) cudaEventDestroy(t->ev_staged);
+    if (t->ev_built) cudaEventDestroy(t->ev_built);
+    std::free(t->async_rec);
     for (int k = 0; k < 3; k++)
         if (t->gs[k]) cudaStreamDestroy(t->gs[k]);
     free_all(t);
