@@ -90,6 +90,7 @@ struct FindSmem {
     int jfail, cover, gstart, gcount, whi, ctot;
     int wcnt[2][C::WARPS];  // per-warp kept counts (scan mode), double-buffered
     int gset, set_lo, set_hi;  // the group's particle set and its index range
+    int split;                 // the unit went to the split pass
 };
 
 struct FindArgs {
@@ -732,17 +733,23 @@ __global__ void __launch_bounds__(C::NT, 1024 / C::NT) k_find(FindArgs A)
     // The wide-shape list runs forward from the start of T.groups, the
     // compact one backward from its end (clamped so that both stay inside).
     int ngroups = A.ngroups;
-    if (ngroups < 0) {
-        const int nf = T.ctr->abort ? 0 : min(T.ctr->ngroups, T.cap_groups);
-        ngroups = A.list == 0 ? nf : (T.ctr->abort ? 0 : min(T.ctr->ngroups_c, T.cap_groups - nf));
+    const int nf0 = T.ctr->abort ? 0 : min(T.ctr->ngroups, T.cap_groups);
+    const int nc0 = T.ctr->abort ? 0 : min(T.ctr->ngroups_c, T.cap_groups - nf0);
+    const int room = T.cap_groups - nf0 - nc0;  // free part of the groups array
+    if (A.list == 2) {
+        ngroups = min(T.ctr->nsplit, room);
+    } else if (ngroups < 0) {
+        ngroups = A.list == 0 ? nf0 : nc0;
     }
-    const int2 *G = A.list == 0 ? T.groups : T.groups + (T.cap_groups - ngroups);
+    const int2 *G = A.list == 0 ? T.groups
+                                : (A.list == 1 ? T.groups + (T.cap_groups - ngroups) : T.groups + nf0);
     const int nchunks = (ngroups + kFindChunk - 1) / kFindChunk;
 
     for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
         const int g1 = min(chunk * kFindChunk + kFindChunk, ngroups);
         for (int g = chunk * kFindChunk; g < g1; g++) {
             __syncthreads();
+            if (A.list == 2 && group_count(G[g].y) == 0) continue;  // placeholder of a split that did not fit
             if (DENS)
                 for (int i = tid; i < kGroupMax * 32; i += C::NT) (&S.qacc[0][0])[i] = 0.0f;
             // ---- queries (warp 0), FP32 only: RN(2h * 2h) is the float
@@ -807,6 +814,24 @@ __global__ void __launch_bounds__(C::NT, 1024 / C::NT) k_find(FindArgs A)
             const long long ctot = S.ctot;
             const long long nset = S.set_hi - S.set_lo;
             const bool scan = ctot > 2 * C::CAP && 3 * nset * C::CAP < 4 * ctot * ctot;
+            // A unit whose candidates need scan mode or many windows is split:
+            // its queries become work units of one query each in the free
+            // part of the groups array, searched by the split pass on many
+            // blocks at once (same lists and densities; one block would
+            // otherwise hold the whole tail of the launch).
+            if ((scan || ctot > 8 * C::CAP) && A.list != 2 && S.gcount > 1) {
+                if (tid == 0) {
+                    const int gc = S.gcount;
+                    const int k = atomicAdd(&T.ctr->nsplit, gc);
+                    const int fit = max(0, min(gc, room - k));
+                    for (int i = 0; i < fit; i++)
+                        T.groups[nf0 + k + i] = make_int2(i < fit && fit == gc ? S.gstart + i : 0,
+                                                          group_pack(S.gset, fit == gc ? 1 : 0));
+                    S.split = fit == gc;  // no room: searched here after all
+                }
+                __syncthreads();
+                if (S.split) continue;
+            }
             if (scan && tid == 0) atomicOr(&T.ctr->status, kStWalk);
             if (scan) group_scan<DENS>(A, S);
 
@@ -926,7 +951,7 @@ static void launch_find_list(const FindArgs &A, int list, int ngroups, int sms, 
     B.ngroups = ngroups;
     if (ngroups == 0) return;
     const bool dens = A.rho != nullptr;
-    long long blocks = (long long)sms * g_find_per_sm[list][dens ? 1 : 0];
+    long long blocks = (long long)sms * g_find_per_sm[list == 1 ? 1 : 0][dens ? 1 : 0];
     if (ngroups > 0) {
         const long long nchunks = (ngroups + kFindChunk - 1) / kFindChunk;
         if (blocks > nchunks) blocks = nchunks;
@@ -976,8 +1001,10 @@ cudaError_t launch_find_rows(FindArgs A, const TreeDev &T, int ngroups, int ngro
         note_launch();
         k_mass_to_tree<<<nb, 256, 0, st>>>(T.spos, m, smass, T.n);
     }
+    cudaMemsetAsync(&T.ctr->nsplit, 0, sizeof(int), st);
     launch_find_list<CfgWide>(A, 0, ngroups, sms, st);
     launch_find_list<CfgCompact>(A, 1, ngroups_c, sms, st);
+    launch_find_list<CfgWide>(A, 2, -1, sms, st);  // the units split above (count on the device)
     return cudaGetLastError();
 }
 

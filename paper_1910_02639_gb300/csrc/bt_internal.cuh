@@ -251,6 +251,7 @@ struct Counters {
     long long hist_need;  // histogram entries a level asked for (on abort)
     int ngroups_c;     // work units of the compact-shape list (end of the groups array)
     int small_next;    // dynamic work counter of the warp builder
+    int nsplit;        // one-query work units made by the search from very wide units
 };
 
 // Per big cell of the current level.
