@@ -54,9 +54,12 @@ typedef enum {
 } bt_status;
 
 /* Stream-ordered device allocator used for the tree's internal buffers.
- * alloc(ctx, bytes, stream) returns a device pointer or NULL;
+ * alloc(ctx, bytes, stream) returns a device pointer or NULL (the call that
+ * needed it then returns BT_ERR_OOM; the handle stays valid and freeable);
  * free(ctx, ptr, stream) releases it.  Pass NULL to use cudaMallocAsync /
- * cudaFreeAsync on the call's stream. */
+ * cudaFreeAsync on the call's stream.  When a handle is rebuilt with a
+ * different allocator (or none), its buffers first go back to the one that
+ * gave them. */
 typedef struct {
     void *ctx;
     void *(*alloc)(void *ctx, size_t bytes, void *stream);
@@ -80,7 +83,8 @@ typedef struct {
  * btree_build -- BuildTree (Algorithm 1) over n particles.
  *
  * x, y, z, h : device, float32 [n], particle positions and smoothing lengths.
- *              Read during the call only (the tree keeps its own copy).
+ *              Read by the build's work on `stream` (the tree keeps its own
+ *              copy); keep them valid until that work has run.
  * n          : 0 <= n < 2^31.
  * bucket_size: s >= 1, the maximum number of particles in a leaf (Table 1).
  * alpha      : fraction of s below which a sub-cell counts as underfull
@@ -105,8 +109,20 @@ typedef struct {
  *  - a cell with more than s particles stays a leaf at depth 32, or when
  *    all its particles fall into one sub-cell whose box equals its own.
  *
- * Synchronises `stream` a few times (once per level of cells with more than
- * 256 particles) to size the next level; returns when the tree is complete.
+ * Synchronous and asynchronous builds.  The first build of a handle (and
+ * any build whose sets or parameters differ from the handle's last
+ * synchronous build) synchronises `stream` a few times (once per level of
+ * cells with more than 256 particles) to size the next level, grows its
+ * buffers if they fall short, and returns when the tree is complete.  A
+ * rebuild of the same sets with the same parameters (new positions) is one
+ * launch of a captured CUDA graph whose level and ratio loops run on the
+ * device, and returns at once (BT_OK) without waiting for the device.  The
+ * searches that follow on `stream` read the tree's work-unit counts on the
+ * device.  The host-side summary of such a rebuild is read by the next call
+ * that needs it (btree_get_info, btree_export, btree_status, the compressed
+ * rows, the next build): a capacity overflow (BT_ERR_CAPACITY; the searches
+ * then write nothing), non-finite input or an oversized leaf of that rebuild
+ * is reported there, and the next build is synchronous again.
  * Errors: BT_ERR_ARG (NULL pointer, n < 0, s < 1, alpha/beta not finite),
  * BT_ERR_NONFINITE (a NaN/Inf coordinate or h, or h < 0), BT_ERR_OOM,
  * BT_ERR_CUDA.  Warning: BT_WARN_OVERSIZED_LEAF.
