@@ -54,7 +54,8 @@ typedef enum {
 } bt_status;
 
 /* Stream-ordered device allocator used for the tree's internal buffers.
- * alloc(ctx, bytes, stream) returns a device pointer or NULL (the call that
+ * alloc(ctx, bytes, stream) returns a device pointer aligned to at least 256
+ * bytes (as cudaMalloc's are), or NULL (the call that
  * needed it then returns BT_ERR_OOM; the handle stays valid and freeable);
  * free(ctx, ptr, stream) releases it.  Pass NULL to use cudaMallocAsync /
  * cudaFreeAsync on the call's stream.  When a handle is rebuilt with a

@@ -439,9 +439,14 @@ __global__ void __launch_bounds__(256) k_big_hist(TreeDev T, LevelBufs L)
         int *hc = hist + c.hist_base;
         const int nc = ncells(c.b, set_dim(T, c.set));
         if (nc > kPrivBins) {
-            for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-                float4 r = src.load_pos(p);
-                atomicAdd(&hc[sub_cell_id(r, w, g, c.b)], 1);
+            // one global atomic per sub-cell and warp (inputs often arrive
+            // in spatial runs: neighbours in a warp share sub-cells)
+            const int lane = threadIdx.x & 31;
+            for (int pb = p0; pb < p1; pb += blockDim.x) {
+                const int p = pb + threadIdx.x;
+                const int j = p < p1 ? sub_cell_id(src.load_pos(p), w, g, c.b) : -1 - lane;
+                const unsigned same = __match_any_sync(~0u, j);
+                if (j >= 0 && (same & ((1u << lane) - 1u)) == 0) atomicAdd(&hc[j], __popc(same));
             }
             continue;
         }
@@ -746,12 +751,21 @@ __global__ void __launch_bounds__(256) k_big_scatter(TreeDev T, LevelBufs L)
         }
         const int nc = ncells(c.b, set_dim(T, c.set));
         if (nc > kPrivBins) {
-            for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-                float4 r;
-                float hh;
-                src.load(p, r, hh);
-                const int j = sub_cell_id(r, w, g, c.b);
-                scatter_one(T, c, j, atomicAdd(&cursor[c.hist_base + j], 1), r, hh, dst_pos, dst_h);
+            // one global atomic per sub-cell and warp; ranks within the warp
+            const int lane = threadIdx.x & 31;
+            for (int pb = p0; pb < p1; pb += blockDim.x) {
+                const int p = pb + threadIdx.x;
+                float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+                float hh = 0.f;
+                if (p < p1) src.load(p, r, hh);
+                const int j = p < p1 ? sub_cell_id(r, w, g, c.b) : -1 - lane;
+                const unsigned same = __match_any_sync(~0u, j);
+                const int lead = __ffs(same) - 1;
+                int at = 0;
+                if (j >= 0 && lane == lead) at = atomicAdd(&cursor[c.hist_base + j], __popc(same));
+                at = __shfl_sync(~0u, at, lead);
+                if (j >= 0)
+                    scatter_one(T, c, j, at + __popc(same & ((1u << lane) - 1u)), r, hh, dst_pos, dst_h);
             }
             continue;
         }
@@ -934,12 +948,14 @@ __global__ void __launch_bounds__(32 * kSmallWarps, 4) k_small(TreeDev T, const 
     const int lane = threadIdx.x & 31;
 
     // cells are taken one at a time from a shared counter (their costs differ
-    // widely), by a grid of as many warps as are resident
+    // widely), by a grid of as many warps as are resident; the next cell's
+    // index is taken while the current one is built
+    int it_next = 0;
+    if (lane == 0) it_next = atomicAdd(&T.ctr->small_next, 1);
     for (;;) {
-        int it = 0;
-        if (lane == 0) it = atomicAdd(&T.ctr->small_next, 1);
-        it = __shfl_sync(~0u, it, 0);
+        const int it = __shfl_sync(~0u, it_next, 0);
         if (it >= nitems) break;
+        if (lane == 0) it_next = atomicAdd(&T.ctr->small_next, 1);
         const SmallItem item = items[it];
         const NodeGeom G = T.geom[item.node];
         const int base = G.start, m0 = G.count;
@@ -969,6 +985,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps, 4) k_small(TreeDev T, const 
             f.eself = m0 <= kWholeMax;
         }
         int sp = 1;
+        bool direct = false;  // particles already written to their final places
         __syncwarp();
         while (sp > 0) {
             Frame &F = S.fr[sp - 1];
@@ -1003,15 +1020,22 @@ __global__ void __launch_bounds__(32 * kSmallWarps, 4) k_small(TreeDev T, const 
                     break;
                 }
                 const int ncell = ncells(b, kd);
-                if (lane == 0)
-                    for (int l = 0; l < 3; l++) F.w[l] = cell_width(g.lo[l], g.hi[l], dim_b(b, kd, l));
-                __syncwarp();
-                // no-progress guard
-                int ne = 0, lj = -1;
-                for (int j = lane; j < ncell; j += 32)
-                    if (hist[j] > 0) { ne++; lj = j; }
+                // no-progress guard; internal sub-cells
+                int ne = 0, lj = -1, nint = 0;
+                for (int j = lane; j < ncell; j += 32) {
+                    const int cnt = hist[j];
+                    if (cnt > 0) { ne++; lj = j; }
+                    nint += cnt > s_set;
+                }
                 ne = warp_sum(ne);
+                nint = F.depth + 1 < kDepthMax ? warp_sum(nint) : 0;
                 for (int o = 16; o > 0; o >>= 1) lj = max(lj, __shfl_xor_sync(~0u, lj, o));
+                // the binary64 sub-cell widths are needed only for child boxes
+                if (ne == 1 || nint > 0) {
+                    if (lane == 0)
+                        for (int l = 0; l < 3; l++) F.w[l] = cell_width(g.lo[l], g.hi[l], dim_b(b, kd, l));
+                    __syncwarp();
+                }
                 bool leaf = false;
                 if (ne == 1) {
                     int cc[3] = {lj % b, (lj / b) % b, lj / (b * b)};
@@ -1146,10 +1170,28 @@ __global__ void __launch_bounds__(32 * kSmallWarps, 4) k_small(TreeDev T, const 
                 }
                 __syncwarp();  // S.hist / S.off are rewritten by the scatter below
                 if (lane == 0) {
-                    NodeWalk w;
-                    make_walk(g, b, slot0, w, kd);
+                    NodeWalk w = S.w;  // made for this b above
+                    w.slot0 = slot0;
                     T.walk[F.node] = w;
                     atomicMax(&T.ctr->max_depth, F.depth + 1);
+                }
+                if (sp == 1 && m0 <= 32 && nint == 0) {
+                    // the whole sub-tree is this node and its leaves: each
+                    // lane moves its one particle straight to its final place
+                    const bool v = lane < m;
+                    const int j = v ? S.key[lane] : ncell + lane;
+                    const unsigned same = __match_any_sync(~0u, j);
+                    if (v) {
+                        const int pos = base + off[j] + __popc(same & ((1u << lane) - 1u));
+                        const int id = S.id[lane];
+                        T.spos[pos] = make_float4(S.x[lane], S.y[lane], S.z[lane], __int_as_float(id));
+                        T.sh[pos] = S.h[lane];
+                        T.inv[id] = pos;
+                    }
+                    direct = true;
+                    sp = 0;
+                    __syncwarp();
+                    break;
                 }
                 // scatter in place: every lane holds its particles in
                 // registers while their new positions are taken
@@ -1201,12 +1243,13 @@ __global__ void __launch_bounds__(32 * kSmallWarps, 4) k_small(TreeDev T, const 
             }
         }
         __syncwarp();
-        for (int k = lane; k < m0; k += 32) {
-            const int id = S.id[k];
-            T.spos[base + k] = make_float4(S.x[k], S.y[k], S.z[k], __int_as_float(id));
-            T.sh[base + k] = S.h[k];
-            T.inv[id] = base + k;
-        }
+        if (!direct)
+            for (int k = lane; k < m0; k += 32) {
+                const int id = S.id[k];
+                T.spos[base + k] = make_float4(S.x[k], S.y[k], S.z[k], __int_as_float(id));
+                T.sh[base + k] = S.h[k];
+                T.inv[id] = base + k;
+            }
         __syncwarp();
     }
 }

@@ -722,6 +722,29 @@ __device__ void group_scan(const FindArgs &A, FindSmem<C> &S)
     }
 }
 
+// The free middle of the groups array: the 8-warp units fill it from the
+// front (nf0 of them), the compact ones from the back; room entries are left.
+__device__ __forceinline__ void free_part(const TreeDev &T, int &nf0, int &room)
+{
+    nf0 = T.ctr->abort ? 0 : min(T.ctr->ngroups, T.cap_groups);
+    const int nc0 = T.ctr->abort ? 0 : min(T.ctr->ngroups_c, T.cap_groups - nf0);
+    room = T.cap_groups - nf0 - nc0;
+}
+
+// Reserve one-query units there for the gc queries of a unit starting at
+// tree position first; false (placeholders of count 0 written) when the
+// free part is full: the unit is then searched whole by its own block.
+__device__ __noinline__ bool split_unit(const TreeDev &T, int first, int gc, int set)
+{
+    int nf0, room;
+    free_part(T, nf0, room);
+    const int k = atomicAdd(&T.ctr->nsplit, gc);
+    const int fit = max(0, min(gc, room - k));
+    for (int i = 0; i < fit; i++)
+        T.groups[nf0 + k + i] = make_int2(fit == gc ? first + i : 0, group_pack(set, fit == gc ? 1 : 0));
+    return fit == gc;
+}
+
 template <class C, bool DENS>
 __global__ void __launch_bounds__(C::NT, 1024 / C::NT) k_find(FindArgs A)
 {
@@ -732,17 +755,21 @@ __global__ void __launch_bounds__(C::NT, 1024 / C::NT) k_find(FindArgs A)
     // ngroups < 0: read the count the build left on the device (graph form).
     // The wide-shape list runs forward from the start of T.groups, the
     // compact one backward from its end (clamped so that both stay inside).
+    // The split pass (list 2) reads the units written into the free middle.
     int ngroups = A.ngroups;
-    const int nf0 = T.ctr->abort ? 0 : min(T.ctr->ngroups, T.cap_groups);
-    const int nc0 = T.ctr->abort ? 0 : min(T.ctr->ngroups_c, T.cap_groups - nf0);
-    const int room = T.cap_groups - nf0 - nc0;  // free part of the groups array
+    const int2 *G;
     if (A.list == 2) {
+        int nf0, room;
+        free_part(T, nf0, room);
         ngroups = min(T.ctr->nsplit, room);
-    } else if (ngroups < 0) {
-        ngroups = A.list == 0 ? nf0 : nc0;
+        G = T.groups + nf0;
+    } else {
+        if (ngroups < 0) {
+            const int nf = T.ctr->abort ? 0 : min(T.ctr->ngroups, T.cap_groups);
+            ngroups = A.list == 0 ? nf : (T.ctr->abort ? 0 : min(T.ctr->ngroups_c, T.cap_groups - nf));
+        }
+        G = A.list == 0 ? T.groups : T.groups + (T.cap_groups - ngroups);
     }
-    const int2 *G = A.list == 0 ? T.groups
-                                : (A.list == 1 ? T.groups + (T.cap_groups - ngroups) : T.groups + nf0);
     const int nchunks = (ngroups + kFindChunk - 1) / kFindChunk;
 
     for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
@@ -820,15 +847,7 @@ __global__ void __launch_bounds__(C::NT, 1024 / C::NT) k_find(FindArgs A)
             // blocks at once (same lists and densities; one block would
             // otherwise hold the whole tail of the launch).
             if ((scan || ctot > 8 * C::CAP) && A.list != 2 && S.gcount > 1) {
-                if (tid == 0) {
-                    const int gc = S.gcount;
-                    const int k = atomicAdd(&T.ctr->nsplit, gc);
-                    const int fit = max(0, min(gc, room - k));
-                    for (int i = 0; i < fit; i++)
-                        T.groups[nf0 + k + i] = make_int2(i < fit && fit == gc ? S.gstart + i : 0,
-                                                          group_pack(S.gset, fit == gc ? 1 : 0));
-                    S.split = fit == gc;  // no room: searched here after all
-                }
+                if (tid == 0) S.split = split_unit(T, S.gstart, S.gcount, S.gset);
                 __syncthreads();
                 if (S.split) continue;
             }
