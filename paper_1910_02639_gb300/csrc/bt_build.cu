@@ -950,7 +950,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps, 4) k_small(TreeDev T, const 
     // cells are taken one at a time from a shared counter (their costs differ
     // widely), by a grid of as many warps as are resident; the next cell's
     // index is taken while the current one is built
-    int it_next = 0;
+    int it_next = 0, mdep = 0;  // mdep: deepest node made by this warp (lane 0)
     if (lane == 0) it_next = atomicAdd(&T.ctr->small_next, 1);
     for (;;) {
         const int it = __shfl_sync(~0u, it_next, 0);
@@ -1030,6 +1030,10 @@ __global__ void __launch_bounds__(32 * kSmallWarps, 4) k_small(TreeDev T, const 
                 ne = warp_sum(ne);
                 nint = F.depth + 1 < kDepthMax ? warp_sum(nint) : 0;
                 for (int o = 16; o > 0; o >>= 1) lj = max(lj, __shfl_xor_sync(~0u, lj, o));
+                // a cell that splits takes its sub-cells' slots now: the
+                // atomic's latency overlaps the scan and the emission below
+                int slot0 = 0;
+                if (lane == 0 && ne != 1) slot0 = atomicAdd(&T.ctr->nslots, ncell);
                 // the binary64 sub-cell widths are needed only for child boxes
                 if (ne == 1 || nint > 0) {
                     if (lane == 0)
@@ -1098,9 +1102,8 @@ __global__ void __launch_bounds__(32 * kSmallWarps, 4) k_small(TreeDev T, const 
                         }
                     }
                 }
-                int slot0 = 0;
                 if (lane == 0) {
-                    slot0 = atomicAdd(&T.ctr->nslots, ncell);
+                    if (ne == 1) slot0 = atomicAdd(&T.ctr->nslots, ncell);
                     if (slot0 + ncell > T.cap_slots) {
                         atomicOr(&T.ctr->status, kStCapSlots);
                         slot0 = -1;
@@ -1173,7 +1176,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps, 4) k_small(TreeDev T, const 
                     NodeWalk w = S.w;  // made for this b above
                     w.slot0 = slot0;
                     T.walk[F.node] = w;
-                    atomicMax(&T.ctr->max_depth, F.depth + 1);
+                    mdep = max(mdep, F.depth + 1);
                 }
                 if (sp == 1 && m0 <= 32 && nint == 0) {
                     // the whole sub-tree is this node and its leaves: each
@@ -1252,6 +1255,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps, 4) k_small(TreeDev T, const 
             }
         __syncwarp();
     }
+    if (lane == 0 && mdep > 0) atomicMax(&T.ctr->max_depth, mdep);
 }
 
 size_t small_smem_bytes(int hist_cells)

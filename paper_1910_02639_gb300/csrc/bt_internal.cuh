@@ -227,12 +227,16 @@ __device__ __forceinline__ float ordered_to_float(int i)
 }
 
 // Device-side counters of one build (one struct in device memory).
+// The counters that every cell's builder updates sit on cache lines of their
+// own, so that their atomics do not queue behind one another.
 struct Counters {
-    int nnodes;        // internal nodes allocated
-    int nslots;        // sub-cells allocated
-    int ngroups;       // find groups emitted
-    int nsmall;        // cells queued for the warp builder
-    int nbig_next;     // big cells queued for the next level
+    alignas(128) int nnodes;     // internal nodes allocated
+    alignas(128) int nslots;     // sub-cells allocated
+    alignas(128) int ngroups;    // find groups emitted
+    alignas(128) int nsmall;     // cells queued for the warp builder
+    alignas(128) int ngroups_c;  // work units of the compact-shape list (end of the groups array)
+    alignas(128) int small_next; // dynamic work counter of the warp builder
+    alignas(128) int nbig_next;  // big cells queued for the next level
     int again;         // some big cell halved b in the last ratio pass
     int max_depth;
     int noversized;
@@ -249,8 +253,6 @@ struct Counters {
     int level_go;      // another level follows
     int abort;         // capacity or input problem: the remaining kernels do nothing
     long long hist_need;  // histogram entries a level asked for (on abort)
-    int ngroups_c;     // work units of the compact-shape list (end of the groups array)
-    int small_next;    // dynamic work counter of the warp builder
     int nsplit;        // one-query work units made by the search from very wide units
 };
 
