@@ -206,7 +206,7 @@ TreeDev view(const btree *t)
     T.cap_groups = t->cap_groups;
     T.cap_small = t->cap_small;
     T.small_hist = small_hist_cells((int)std::max<int64_t>(t->s, 1));
-    T.pad_t = 0;
+    T.tiny_hist = small_hist_cells((int)std::max<int64_t>(t->s, 1), kTinyCap);
     return T;
 }
 
@@ -233,7 +233,7 @@ int ensure_particle_caps(btree *t, int64_t n)
         t->cap_groups = (int)want_groups;
     }
     if (t->cap_small < want_small) {
-        if (!realloc_dev(t, t->small, 0, want_small, false)) return BT_ERR_OOM;
+        if (!realloc_dev(t, t->small, 0, 2 * want_small, false)) return BT_ERR_OOM;  // two queues
         t->cap_small = (int)want_small;
     }
     if (t->cap_big < want_big) {
@@ -327,6 +327,7 @@ LevelBufs lview(const btree *t, const float *x, const float *y, const float *z, 
     L.cursor = t->cursor;
     L.tiles = t->tiles;
     L.small = t->small;
+    L.tiny = t->small ? t->small + t->cap_small : nullptr;
     L.cap_hist = t->cap_hist;
     L.cap_big = t->cap_big;
     L.cap_tiles = scan_tile_count(t->cap_hist);
@@ -413,7 +414,9 @@ int do_build(btree *t, const float *x, const float *y, const float *z, const flo
         launch_level_finish(T, L, H, t->sms, 0, 0, st);
         if ((rc = read_counters(t, st)) != BT_OK) return rc;
     }
-    if (!t->hctr->abort) launch_small(T, L, std::min(t->hctr->nsmall, t->cap_small), t->sms, st);
+    if (!t->hctr->abort)
+        launch_small(T, L, std::min(t->hctr->nsmall, t->cap_small), std::min(t->hctr->ntiny, t->cap_small),
+                     t->sms, st);
     cudaEventRecord(t->ev1, st);
     if ((rc = read_counters(t, st)) != BT_OK) return rc;
     return finish_build(t, st);
@@ -489,7 +492,7 @@ cudaError_t capture_step(btree *t, const GraphKey &K, cudaGraph_t *out)
             chk(cudaStreamEndCapture(s1, &lbody));
         }
     }
-    launch_small(T, L, t->cap_small, t->sms, s0);
+    launch_small(T, L, t->cap_small, t->cap_small, t->sms, s0);
     record_event(t->ev1, s0, true);
     if (!K.nbrs) {
         // the build alone: counters to mapped host memory, then its event
@@ -513,9 +516,10 @@ uint64_t graph_launches(const Counters &c, bool find, bool dens)
 {
     // head: init_counters, init_sets, bbox, root_sets, copy_leaf_roots, level_go;
     // per level: begin, setup, scan, zero, finish, 3 scans, emit, scatter, level_go;
-    // per ratio pass: hist, count, decide, zero, ratio_end; then small and find
-    // (find: the two work-unit lists and the pass over the units split by them)
-    return 6 + 11 * (uint64_t)c.level + 5 * (uint64_t)c.ratio_total + 1 + (find ? 3 + (dens ? 1 : 0) : 0);
+    // per ratio pass: hist, count, decide, zero, ratio_end; then the two warp
+    // builders and find (find: the two work-unit lists and the pass over the
+    // units split by them)
+    return 6 + 11 * (uint64_t)c.level + 5 * (uint64_t)c.ratio_total + 2 + (find ? 3 + (dens ? 1 : 0) : 0);
 }
 
 // Launches the captured step (captured again when a pointer or size
@@ -654,7 +658,7 @@ static int build_core(btree *t, const float *x, const float *y, const float *z, 
         int64_t cs = std::min<int64_t>((int64_t)t->cap_slots * 2, INT32_MAX / 2);
         int64_t cm = std::min<int64_t>((int64_t)t->cap_small * 2 + 1024, INT32_MAX / 2);
         if (!realloc_dev(t, t->geom, 0, cn, false) || !realloc_dev(t, t->walk, 0, cn, false) ||
-            !realloc_dev(t, t->slots, 0, cs, false) || !realloc_dev(t, t->small, 0, cm, false)) {
+            !realloc_dev(t, t->slots, 0, cs, false) || !realloc_dev(t, t->small, 0, 2 * cm, false)) {
             rc = BT_ERR_OOM;
             break;
         }

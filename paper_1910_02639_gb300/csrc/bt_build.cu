@@ -56,22 +56,38 @@ __device__ __forceinline__ int warp_atomic_add(int *p, int v)
 // kernels, one thread per sub-cell, thousands of calls per launch); the
 // per-warp small-cell builder takes plain atomics (a few calls per cell;
 // aggregating them there gave no measurable gain).
-template <bool kWarpAgg = false>
-__device__ __forceinline__ void emit_groups(const TreeDev &T, int set, int start, int cnt)
+// The counter of a set's list of work units.
+__device__ __forceinline__ int *group_counter(const TreeDev &T, int set)
+{
+    return (T.set_flags[set] & kSetFindCompact) ? &T.ctr->ngroups_c : &T.ctr->ngroups;
+}
+
+// Write the work units of [start, start + cnt) at list entries g0, g0 + 1, ...
+// (reserved on the set's counter).
+__device__ __forceinline__ void emit_write(const TreeDev &T, int set, int g0, int start, int cnt)
 {
     const int gm = T.set_gmax[set];
     const int ng = (cnt + gm - 1) / gm;
     const bool compact = (T.set_flags[set] & kSetFindCompact) != 0;
-    int *ctr = compact ? &T.ctr->ngroups_c : &T.ctr->ngroups;
-    const int g0 = kWarpAgg
-                       ? group_atomic_add(cg::labeled_partition(cg::coalesced_threads(), (int)compact), ctr, ng)
-                       : atomicAdd(ctr, ng);
     for (int q = 0; q < ng; q++) {
         if (g0 + q >= T.cap_groups) break;
         const int idx = compact ? T.cap_groups - 1 - (g0 + q) : g0 + q;
         T.groups[idx] = make_int2(start + q * gm, group_pack(set, min(gm, cnt - q * gm)));
     }
     if (g0 + ng > T.cap_groups) atomicOr(&T.ctr->status, kStCapGroups);
+}
+
+template <bool kWarpAgg = false>
+__device__ __forceinline__ void emit_groups(const TreeDev &T, int set, int start, int cnt)
+{
+    const int gm = T.set_gmax[set];
+    const int ng = (cnt + gm - 1) / gm;
+    const bool compact = (T.set_flags[set] & kSetFindCompact) != 0;
+    int *ctr = group_counter(T, set);
+    const int g0 = kWarpAgg
+                       ? group_atomic_add(cg::labeled_partition(cg::coalesced_threads(), (int)compact), ctr, ng)
+                       : atomicAdd(ctr, ng);
+    emit_write(T, set, g0, start, cnt);
 }
 
 __device__ __forceinline__ int set_b0(const TreeDev &T, int set, int count)
@@ -193,8 +209,9 @@ __device__ void root_set(TreeDev &T, int s, const LevelBufs &L)
         T.set_flags[s] |= kSetLeafRoot;
         emit_groups(T, s, start, n);
     } else if (n <= kSmallCap) {
-        const int k = atomicAdd(&T.ctr->nsmall, 1);
-        if (k < T.cap_small) L.small[k] = SmallItem{s, 2};
+        const bool tiny = n <= kTinyCap;
+        const int k = atomicAdd(tiny ? &T.ctr->ntiny : &T.ctr->nsmall, 1);
+        if (k < T.cap_small) (tiny ? L.tiny : L.small)[k] = SmallItem{s, 2};
         else atomicOr(&T.ctr->status, kStCapSmall);
     } else {
         const int k = atomicAdd(&T.ctr->nbig_next, 1);
@@ -665,9 +682,13 @@ __global__ void __launch_bounds__(256) k_big_emit(TreeDev T, LevelBufs L)
                         atomicOr(&T.ctr->status, kStCapBig);
                         T.ctr->abort = 1;
                     }
-                } else {
+                } else if (cnt > kTinyCap) {
                     int k = warp_atomic_add(&T.ctr->nsmall, 1);
                     if (k < T.cap_small) small[k] = SmallItem{child, dst_buf};
+                    else atomicOr(&T.ctr->status, kStCapSmall);
+                } else {
+                    int k = warp_atomic_add(&T.ctr->ntiny, 1);
+                    if (k < T.cap_small) L.tiny[k] = SmallItem{child, dst_buf};
                     else atomicOr(&T.ctr->status, kStCapSmall);
                 }
             }
@@ -898,31 +919,33 @@ struct Frame {
 
 constexpr int kSmallWarps = 4;
 constexpr int kHistMax = 512;  // >= b0^k for any cell of <= kSmallCap particles and s >= 1
-static_assert(kSmallCap % 32 == 0, "whole particles per lane");
+constexpr int kTinyHistMax = 64;  // the same for <= kTinyCap particles (s = 1: b = 4)
+static_assert(kSmallCap % 32 == 0 && kTinyCap % 32 == 0, "whole particles per lane");
 
-// Per warp; the warps' histograms (2 x T.small_hist ints each: counts and
-// offsets) follow the kSmallWarps records.
+// Per warp; the warps' histograms (2 x hist ints each: counts and offsets)
+// follow the kSmallWarps records.
+template <int CAP>
 struct SmallSmem {
-    float x[kSmallCap], y[kSmallCap], z[kSmallCap];  // one array per field, so that
-    int id[kSmallCap];                                 // the in-place scatter moves one
-    float h[kSmallCap];                                // field at a time
-    short key[kSmallCap];
+    float x[CAP], y[CAP], z[CAP];  // one array per field, so that
+    int id[CAP];                   // the in-place scatter moves one
+    float h[CAP];                  // field at a time
+    short key[CAP];
     Frame fr[kDepthMax + 2];
     NodeWalk w;
 };
 
 // v[pos[k]] = v[k] for k < m (pos a permutation of 0..m-1), in place: each
-// lane holds its (at most kSmallCap / 32) values in registers meanwhile.
-template <class V>
+// lane holds its (at most CAP / 32) values in registers meanwhile.
+template <int CAP, class V>
 __device__ __forceinline__ void permute_field(V *v, const short *pos, int m, int lane)
 {
-    V r[kSmallCap / 32];
+    V r[CAP / 32];
 #pragma unroll
-    for (int q = 0; q < kSmallCap / 32; q++)
+    for (int q = 0; q < CAP / 32; q++)
         if (lane + 32 * q < m) r[q] = v[lane + 32 * q];
     __syncwarp();
 #pragma unroll
-    for (int q = 0; q < kSmallCap / 32; q++)
+    for (int q = 0; q < CAP / 32; q++)
         if (lane + 32 * q < m) v[pos[lane + 32 * q]] = r[q];
     __syncwarp();
 }
@@ -933,35 +956,43 @@ __device__ __forceinline__ int warp_sum(int v)
     return v;
 }
 
-// One warp builds the whole sub-tree of one cell of <= kSmallCap particles.
-__global__ void __launch_bounds__(32 * kSmallWarps, 4) k_small(TreeDev T, const SmallItem *items,
-                                                            Src src0, Src src1, Src srcin)
+// One warp builds the whole sub-tree of one cell of <= CAP particles: an
+// instance for cells of up to kSmallCap particles and a leaner one (fewer
+// registers and less shared memory: 24 warps per SM instead of 16) for the many
+// cells of up to kTinyCap.
+template <int CAP>
+__global__ void __launch_bounds__(32 * kSmallWarps, CAP == kTinyCap ? 6 : 4)
+    k_small(TreeDev T, const SmallItem *items, Src src0, Src src1, Src srcin)
 {
     if (T.ctr->abort) return;
-    const int nitems = min(T.ctr->nsmall, T.cap_small);
+    constexpr bool kTiny = CAP == kTinyCap;
+    const int nitems = min(kTiny ? T.ctr->ntiny : T.ctr->nsmall, T.cap_small);
+    int *const next_ctr = kTiny ? &T.ctr->tiny_next : &T.ctr->small_next;
+    const int hcells = kTiny ? T.tiny_hist : T.small_hist;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int wid = threadIdx.x >> 5;
-    SmallSmem &S = reinterpret_cast<SmallSmem *>(smem_raw)[wid];
-    int *const hist = reinterpret_cast<int *>(smem_raw + kSmallWarps * sizeof(SmallSmem)) +
-                      wid * 2 * T.small_hist;
-    int *const off = hist + T.small_hist;
+    SmallSmem<CAP> &S = reinterpret_cast<SmallSmem<CAP> *>(smem_raw)[wid];
+    int *const hist = reinterpret_cast<int *>(smem_raw + kSmallWarps * sizeof(SmallSmem<CAP>)) +
+                      wid * 2 * hcells;
+    int *const off = hist + hcells;
     const int lane = threadIdx.x & 31;
 
     // cells are taken one at a time from a shared counter (their costs differ
     // widely), by a grid of as many warps as are resident; the next cell's
     // index is taken while the current one is built
     int it_next = 0, mdep = 0;  // mdep: deepest node made by this warp (lane 0)
-    if (lane == 0) it_next = atomicAdd(&T.ctr->small_next, 1);
+    if (lane == 0) it_next = atomicAdd(next_ctr, 1);
     for (;;) {
         const int it = __shfl_sync(~0u, it_next, 0);
         if (it >= nitems) break;
-        if (lane == 0) it_next = atomicAdd(&T.ctr->small_next, 1);
+        if (lane == 0) it_next = atomicAdd(next_ctr, 1);
         const SmallItem item = items[it];
         const NodeGeom G = T.geom[item.node];
         const int base = G.start, m0 = G.count;
         const int set = G.set;
         const int s_set = T.set_s[set];
         const int na = T.set_na[set];
+        const int gm_set = T.set_gmax[set];
         const bool octree = (T.set_flags[set] & kSetOctree) != 0;
         const bool pack = (T.set_flags[set] & kSetPackLeaves) != 0;
         const int kd = set_dim(T, set);
@@ -1032,8 +1063,12 @@ __global__ void __launch_bounds__(32 * kSmallWarps, 4) k_small(TreeDev T, const 
                 for (int o = 16; o > 0; o >>= 1) lj = max(lj, __shfl_xor_sync(~0u, lj, o));
                 // a cell that splits takes its sub-cells' slots now: the
                 // atomic's latency overlaps the scan and the emission below
-                int slot0 = 0;
-                if (lane == 0 && ne != 1) slot0 = atomicAdd(&T.ctr->nslots, ncell);
+                // (and, when it is one work unit, that unit's list entry)
+                int slot0 = 0, ge = -1;
+                if (lane == 0 && ne != 1) {
+                    slot0 = atomicAdd(&T.ctr->nslots, ncell);
+                    if (F.eself && m <= gm_set) ge = atomicAdd(group_counter(T, set), 1);
+                }
                 // the binary64 sub-cell widths are needed only for child boxes
                 if (ne == 1 || nint > 0) {
                     if (lane == 0)
@@ -1083,8 +1118,9 @@ __global__ void __launch_bounds__(32 * kSmallWarps, 4) k_small(TreeDev T, const 
                 __syncwarp();
                 // a cell of <= kWholeMax particles becomes work units of its own
                 if (F.eself && lane == 0) {
-                    if (m <= T.set_gmax[set]) {
-                        emit_groups(T, set, base + a, m);
+                    if (m <= gm_set) {
+                        if (ge >= 0) emit_write(T, set, ge, base + a, m);
+                        else emit_groups(T, set, base + a, m);
                     } else {
                         // two units split at the sub-cell boundary nearest the
                         // middle (sub-cell ids run x fastest: low ids are low z)
@@ -1203,11 +1239,11 @@ __global__ void __launch_bounds__(32 * kSmallWarps, 4) k_small(TreeDev T, const 
                 for (int k = lane; k < m; k += 32)
                     S.key[a + k] = (short)atomicAdd(&hist[S.key[a + k]], 1);  // now the position
                 __syncwarp();
-                permute_field(S.x + a, S.key + a, m, lane);
-                permute_field(S.y + a, S.key + a, m, lane);
-                permute_field(S.z + a, S.key + a, m, lane);
-                permute_field(S.h + a, S.key + a, m, lane);
-                permute_field(S.id + a, S.key + a, m, lane);
+                permute_field<CAP>(S.x + a, S.key + a, m, lane);
+                permute_field<CAP>(S.y + a, S.key + a, m, lane);
+                permute_field<CAP>(S.z + a, S.key + a, m, lane);
+                permute_field<CAP>(S.h + a, S.key + a, m, lane);
+                permute_field<CAP>(S.id + a, S.key + a, m, lane);
                 if (lane == 0) { F.b = b; F.slot0 = slot0; F.next = 0; }
                 __syncwarp();
             } else {
@@ -1258,9 +1294,10 @@ __global__ void __launch_bounds__(32 * kSmallWarps, 4) k_small(TreeDev T, const 
     if (lane == 0 && mdep > 0) atomicMax(&T.ctr->max_depth, mdep);
 }
 
-size_t small_smem_bytes(int hist_cells)
+size_t small_smem_bytes(int hist_cells, int cap)
 {
-    return (sizeof(SmallSmem) + 2 * sizeof(int) * (size_t)hist_cells) * kSmallWarps;
+    const size_t rec = cap == kTinyCap ? sizeof(SmallSmem<kTinyCap>) : sizeof(SmallSmem<kSmallCap>);
+    return (rec + 2 * sizeof(int) * (size_t)hist_cells) * kSmallWarps;
 }
 
 // ------------------------------------------------------------------ host side
@@ -1354,19 +1391,21 @@ void launch_level_finish(const TreeDev &T, const LevelBufs &L, const LevelHints 
 
 int scan_tile_count(long long n) { return (int)((n + kScanTile - 1) / kScanTile) + 1; }
 
-void launch_small(const TreeDev &T, const LevelBufs &L, long long nitems_hint, int sms, cudaStream_t st)
+template <int CAP>
+static void launch_small_cap(const TreeDev &T, const LevelBufs &L, long long nitems_hint, int sms,
+                             cudaStream_t st)
 {
     if (nitems_hint <= 0) return;
     const Src s0{nullptr, nullptr, nullptr, nullptr, L.wpos[0], L.wh[0]};
     const Src s1{nullptr, nullptr, nullptr, nullptr, L.wpos[1], L.wh[1]};
-    const size_t smem = small_smem_bytes(T.small_hist);
+    const size_t smem = small_smem_bytes(CAP == kTinyCap ? T.tiny_hist : T.small_hist, CAP);
     // as many blocks as are resident at once (the warps take cells from a
     // counter until none is left)
     static thread_local size_t occ_smem = 0;
     static thread_local int occ_blocks = 0;
     if (occ_smem != smem) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small, 32 * kSmallWarps, smem) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small<CAP>, 32 * kSmallWarps, smem) !=
                 cudaSuccess ||
             per_sm < 1) {
             cudaGetLastError();
@@ -1377,13 +1416,23 @@ void launch_small(const TreeDev &T, const LevelBufs &L, long long nitems_hint, i
     }
     const int blocks = grid_for(nitems_hint, kSmallWarps, sms * occ_blocks);
     note_launch();
-    k_small<<<blocks, 32 * kSmallWarps, smem, st>>>(T, L.small, s0, s1, L.in);
+    k_small<CAP><<<blocks, 32 * kSmallWarps, smem, st>>>(T, CAP == kTinyCap ? L.tiny : L.small, s0, s1, L.in);
+}
+
+void launch_small(const TreeDev &T, const LevelBufs &L, long long nsmall_hint, long long ntiny_hint, int sms,
+                  cudaStream_t st)
+{
+    launch_small_cap<kTinyCap>(T, L, ntiny_hint, sms, st);
+    launch_small_cap<kSmallCap>(T, L, nsmall_hint, sms, st);
 }
 
 cudaError_t build_init_attributes()
 {
-    return cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)small_smem_bytes(kHistMax));
+    cudaError_t e = cudaFuncSetAttribute(k_small<kSmallCap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)small_smem_bytes(kHistMax, kSmallCap));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_small<kTinyCap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)small_smem_bytes(kTinyHistMax, kTinyCap));
 }
 
 // One thread: copy the counters (and node 0's b) into the mapped host mirror.

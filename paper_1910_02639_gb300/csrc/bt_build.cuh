@@ -27,9 +27,11 @@ void launch_ratio_pass(const TreeDev &T, const LevelBufs &L, const LevelHints &H
                        cudaGraphConditionalHandle hratio, int graph, cudaStream_t st);
 void launch_level_finish(const TreeDev &T, const LevelBufs &L, const LevelHints &H, int sms,
                          cudaGraphConditionalHandle hlevel, int graph, cudaStream_t st);
-void launch_small(const TreeDev &T, const LevelBufs &L, long long nitems_hint, int sms, cudaStream_t st);
+// The warp builders: cells of <= kTinyCap particles, then the rest up to kSmallCap.
+void launch_small(const TreeDev &T, const LevelBufs &L, long long nsmall_hint, long long ntiny_hint, int sms,
+                  cudaStream_t st);
 int scan_tile_count(long long n);
-size_t small_smem_bytes(int hist_cells);
+size_t small_smem_bytes(int hist_cells, int cap);
 // Small read-backs into mapped pinned host memory (see Readback).
 void launch_readback(const Counters *ctr, const NodeWalk *walk0, Readback *out, cudaStream_t st);
 void launch_readback_total(const long long *total, Readback *out, cudaStream_t st);

@@ -16,6 +16,7 @@ constexpr int kDepthMax = 32;   // a cell at depth 32 is never split
 constexpr int kGroupMax = 32;   // most particles per find work unit (per set: 1..32)
 constexpr int kWholeMax = 32;   // cells up to this size become one work unit
 constexpr int kSmallCap = 256;  // cells up to this size are built by one warp in smem
+constexpr int kTinyCap = 32;    // ... by a leaner instance of the warp builder up to this size
 constexpr int kBigChunk = 4096; // particles per block in the per-level big-cell passes
 constexpr int kRootChunk = 4096; // particles per block in the root passes (one set per block)
 
@@ -236,6 +237,8 @@ struct Counters {
     alignas(128) int nsmall;     // cells queued for the warp builder
     alignas(128) int ngroups_c;  // work units of the compact-shape list (end of the groups array)
     alignas(128) int small_next; // dynamic work counter of the warp builder
+    alignas(128) int ntiny;      // cells of <= kTinyCap particles queued for the warp builder
+    alignas(128) int tiny_next;  // their dynamic work counter
     alignas(128) int nbig_next;  // big cells queued for the next level
     int again;         // some big cell halved b in the last ratio pass
     int max_depth;
@@ -327,16 +330,16 @@ struct TreeDev {
     Counters *ctr;
     int cap_nodes, cap_slots, cap_groups, cap_small;
     int small_hist;  // histogram entries per warp of the small-cell builder (>= b0^k at kSmallCap)
-    int pad_t;
+    int tiny_hist;   // the same at kTinyCap
 };
 
-// Largest b^k that any cell of at most kSmallCap particles starts from, over
+// Largest b^k that any cell of at most cap particles starts from, over
 // sets whose bucket size is at least smin (Eq. 1 is monotone in n and in 1/s;
 // the ratio test only lowers b).
-__host__ __device__ __forceinline__ int small_hist_cells(int smin)
+__host__ __device__ __forceinline__ int small_hist_cells(int smin, int cap = kSmallCap)
 {
-    int c = ncells(branching_factor(kSmallCap, smin), 3);
-    c = c > ncells(branching_factor2(kSmallCap, smin), 2) ? c : ncells(branching_factor2(kSmallCap, smin), 2);
+    int c = ncells(branching_factor(cap, smin), 3);
+    c = c > ncells(branching_factor2(cap, smin), 2) ? c : ncells(branching_factor2(cap, smin), 2);
     c = c > 8 ? c : 8;  // octree
     return (c + 3) & ~3;
 }
@@ -420,7 +423,8 @@ struct LevelBufs {
     int *ids[2];
     BigCell *big;
     int *hist, *hoff, *cursor, *tiles;
-    SmallItem *small;
+    SmallItem *small;  // cells of kTinyCap < n <= kSmallCap particles
+    SmallItem *tiny;   // cells of n <= kTinyCap (both queues hold cap_small items)
     long long cap_hist;
     int cap_big, cap_tiles;
 };
