@@ -102,54 +102,68 @@ __device__ __forceinline__ int set_b0(const TreeDev &T, int set, int count)
 // every coordinate and h is finite and h >= 0.
 // One block per kRootChunk particles of one set: coalesced loads, a block
 // reduction, six atomics per block.
+// Block-wide min/max of v (6 values) into the set's bounding box.
+__device__ __forceinline__ void bbox_flush(const TreeDev &T, int set, float (&v)[6], float (&red)[6][8])
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 6; k++) {
+            const float w = __shfl_xor_sync(~0u, v[k], o);
+            v[k] = k < 3 ? fminf(v[k], w) : fmaxf(v[k], w);
+        }
+    __syncthreads();  // red of the previous flush
+    if (lane == 0)
+        for (int k = 0; k < 6; k++) red[k][warp] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int k = 0; k < 6; k++) {
+            float w = lane < nw ? red[k][lane] : (k < 3 ? FLT_MAX : -FLT_MAX);
+            for (int o = 4; o > 0; o >>= 1) {
+                const float u = __shfl_xor_sync(~0u, w, o);
+                w = k < 3 ? fminf(w, u) : fmaxf(w, u);
+            }
+            if (lane == 0) {
+                int *bb = T.set_bbox + 6 * set + k;
+                if (k < 3) atomicMin(bb, float_to_ordered(w));
+                else atomicMax(bb, float_to_ordered(w));
+            }
+        }
+    }
+}
+
+// The box is kept in registers over consecutive chunks of one set and
+// added to the set's box once per set and block (a large set's chunks
+// would otherwise all take atomics on the same six words).
 __global__ void __launch_bounds__(256) k_bbox(TreeDev T, const float *__restrict__ x,
                                               const float *__restrict__ y,
                                               const float *__restrict__ z,
                                               const float *__restrict__ h)
 {
     __shared__ float red[6][8];
-    __shared__ int s_set;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int total = T.set_chunk0[T.nsets];
     bool bad = false;
+    int cur = -1;
+    float v[6] = {FLT_MAX, FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
     for (int c = blockIdx.x; c < total; c += gridDim.x) {
-        __syncthreads();  // red / s_set of the previous block step
-        if (tid == 0) s_set = set_of_chunk(T.set_chunk0, T.nsets, c);
-        __syncthreads();
-        const int set = s_set;
+        const int set = set_of_chunk(T.set_chunk0, T.nsets, c);  // the same in the whole block
+        if (set != cur) {
+            if (cur >= 0) bbox_flush(T, cur, v, red);
+            cur = set;
+            for (int k = 0; k < 6; k++) v[k] = k < 3 ? FLT_MAX : -FLT_MAX;
+        }
         const int p0 = T.set_start[set] + (c - T.set_chunk0[set]) * kRootChunk;
         const int p1 = min(p0 + kRootChunk, T.set_start[set + 1]);
-        float v[6] = {FLT_MAX, FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
+#pragma unroll 4
         for (int p = p0 + tid; p < p1; p += blockDim.x) {
             const float a = x[p], b = y[p], cc = z[p], hh = h[p];
             bad |= !isfinite(a) || !isfinite(b) || !isfinite(cc) || !isfinite(hh) || !(hh >= 0.0f);
             v[0] = fminf(v[0], a); v[1] = fminf(v[1], b); v[2] = fminf(v[2], cc);
             v[3] = fmaxf(v[3], a); v[4] = fmaxf(v[4], b); v[5] = fmaxf(v[5], cc);
         }
-        for (int o = 16; o > 0; o >>= 1)
-            for (int k = 0; k < 6; k++) {
-                const float w = __shfl_xor_sync(~0u, v[k], o);
-                v[k] = k < 3 ? fminf(v[k], w) : fmaxf(v[k], w);
-            }
-        if (lane == 0)
-            for (int k = 0; k < 6; k++) red[k][warp] = v[k];
-        __syncthreads();
-        if (warp == 0) {
-            const int nw = blockDim.x >> 5;
-            for (int k = 0; k < 6; k++) {
-                float w = lane < nw ? red[k][lane] : (k < 3 ? FLT_MAX : -FLT_MAX);
-                for (int o = 4; o > 0; o >>= 1) {
-                    const float u = __shfl_xor_sync(~0u, w, o);
-                    w = k < 3 ? fminf(w, u) : fmaxf(w, u);
-                }
-                if (lane == 0) {
-                    int *bb = T.set_bbox + 6 * set + k;
-                    if (k < 3) atomicMin(bb, float_to_ordered(w));
-                    else atomicMax(bb, float_to_ordered(w));
-                }
-            }
-        }
     }
+    if (cur >= 0) bbox_flush(T, cur, v, red);
     if (__any_sync(~0u, bad) && lane == 0) atomicOr(&T.ctr->status, kStNonfinite);
 }
 
@@ -434,7 +448,7 @@ __device__ __forceinline__ int sub_cell_id(const float4 &p, const NodeWalk &w, c
 constexpr int kPrivBins = 4096;
 static_assert(kPrivBins <= 4096 && kBigChunk <= 4096, "sub-cell and rank packed in 12 bits each");
 
-__global__ void __launch_bounds__(256) k_big_hist(TreeDev T, LevelBufs L)
+__global__ void __launch_bounds__(256, 4) k_big_hist(TreeDev T, LevelBufs L)
 {
     __shared__ int sh_bin[kPrivBins];
     const Counters *ctr = T.ctr;
@@ -457,13 +471,22 @@ __global__ void __launch_bounds__(256) k_big_hist(TreeDev T, LevelBufs L)
         const int nc = ncells(c.b, set_dim(T, c.set));
         if (nc > kPrivBins) {
             // one global atomic per sub-cell and warp (inputs often arrive
-            // in spatial runs: neighbours in a warp share sub-cells)
+            // in spatial runs: neighbours in a warp share sub-cells); two
+            // particles per thread and step, so that twice the loads are in
+            // flight
             const int lane = threadIdx.x & 31;
-            for (int pb = p0; pb < p1; pb += blockDim.x) {
-                const int p = pb + threadIdx.x;
-                const int j = p < p1 ? sub_cell_id(src.load_pos(p), w, g, c.b) : -1 - lane;
-                const unsigned same = __match_any_sync(~0u, j);
-                if (j >= 0 && (same & ((1u << lane) - 1u)) == 0) atomicAdd(&hc[j], __popc(same));
+            for (int pb = p0; pb < p1; pb += 2 * blockDim.x) {
+                const int pa = pb + threadIdx.x, pc = pa + blockDim.x;
+                float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rc = ra;
+                if (pa < p1) ra = src.load_pos(pa);
+                if (pc < p1) rc = src.load_pos(pc);
+                const int ja = pa < p1 ? sub_cell_id(ra, w, g, c.b) : -1 - lane;
+                const int jc = pc < p1 ? sub_cell_id(rc, w, g, c.b) : -1 - lane;
+                const unsigned sa = __match_any_sync(~0u, ja);
+                const unsigned sc = __match_any_sync(~0u, jc);
+                const unsigned lt = (1u << lane) - 1u;
+                if (ja >= 0 && (sa & lt) == 0) atomicAdd(&hc[ja], __popc(sa));
+                if (jc >= 0 && (sc & lt) == 0) atomicAdd(&hc[jc], __popc(sc));
             }
             continue;
         }
@@ -491,6 +514,8 @@ __global__ void __launch_bounds__(256) k_big_count(TreeDev T, LevelBufs L)
     const int total = ctr->hist_total;
     BigCell *big = L.big;
     const int *hist = L.hist;
+    __shared__ int s_red[4][8];  // per warp: cell (or -2: mixed), u, ne, last j
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int e0 = blockIdx.x * blockDim.x; e0 < total; e0 += gridDim.x * blockDim.x) {
         const int e = e0 + threadIdx.x;
         int ci = -1, u = 0, ne = 0, lj = -1;
@@ -507,8 +532,10 @@ __global__ void __launch_bounds__(256) k_big_count(TreeDev T, LevelBufs L)
                 ci = -1;
             }
         }
-        // one atomic per warp when the whole warp lies in one cell (the
-        // common case: cells are long contiguous runs of e), else per lane
+        // one atomic per block when the whole block lies in one cell (the
+        // common case: cells are long contiguous runs of e; a level with one
+        // huge cell would otherwise put every warp's atomics on one line),
+        // else one per warp, else per lane
         const unsigned same = __match_any_sync(~0u, ci);
         if (same == 0xffffffffu) {
             int su = u, sne = ne, slj = lj;
@@ -517,16 +544,41 @@ __global__ void __launch_bounds__(256) k_big_count(TreeDev T, LevelBufs L)
                 sne += __shfl_xor_sync(~0u, sne, o);
                 slj = max(slj, __shfl_xor_sync(~0u, slj, o));
             }
-            if (ci >= 0 && (threadIdx.x & 31) == 0) {
-                if (su) atomicAdd(&big[ci].u, su);
-                if (sne) atomicAdd(&big[ci].ne, sne);
-                if (slj >= 0) atomicMax(&big[ci].lastj, slj);
+            if (lane == 0) { s_red[0][warp] = ci; s_red[1][warp] = su; s_red[2][warp] = sne; s_red[3][warp] = slj; }
+        } else {
+            if (lane == 0) s_red[0][warp] = -2;
+            if (ci >= 0) {
+                if (u) atomicAdd(&big[ci].u, u);
+                if (ne) atomicAdd(&big[ci].ne, ne);
+                if (lj >= 0) atomicMax(&big[ci].lastj, lj);
             }
-        } else if (ci >= 0) {
-            if (u) atomicAdd(&big[ci].u, u);
-            if (ne) atomicAdd(&big[ci].ne, ne);
-            if (lj >= 0) atomicMax(&big[ci].lastj, lj);
         }
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = blockDim.x >> 5;
+            const int wc = lane < nw ? s_red[0][lane] : -1;
+            const int c0 = __shfl_sync(~0u, wc, 0);
+            const bool one = __all_sync(~0u, lane >= nw || wc == c0) && c0 >= 0;
+            if (one) {  // every warp of the block in cell c0
+                int su = lane < nw ? s_red[1][lane] : 0, sne = lane < nw ? s_red[2][lane] : 0;
+                int slj = lane < nw ? s_red[3][lane] : -1;
+                for (int o = 4; o > 0; o >>= 1) {
+                    su += __shfl_xor_sync(~0u, su, o);
+                    sne += __shfl_xor_sync(~0u, sne, o);
+                    slj = max(slj, __shfl_xor_sync(~0u, slj, o));
+                }
+                if (lane == 0) {
+                    if (su) atomicAdd(&big[c0].u, su);
+                    if (sne) atomicAdd(&big[c0].ne, sne);
+                    if (slj >= 0) atomicMax(&big[c0].lastj, slj);
+                }
+            } else if (lane < nw && wc >= 0) {  // per warp
+                if (s_red[1][lane]) atomicAdd(&big[wc].u, s_red[1][lane]);
+                if (s_red[2][lane]) atomicAdd(&big[wc].ne, s_red[2][lane]);
+                if (s_red[3][lane] >= 0) atomicMax(&big[wc].lastj, s_red[3][lane]);
+            }
+        }
+        __syncthreads();  // s_red is reused by the next step
     }
 }
 
@@ -772,21 +824,29 @@ __global__ void __launch_bounds__(256) k_big_scatter(TreeDev T, LevelBufs L)
         }
         const int nc = ncells(c.b, set_dim(T, c.set));
         if (nc > kPrivBins) {
-            // one global atomic per sub-cell and warp; ranks within the warp
+            // one global atomic per sub-cell and warp; ranks within the warp;
+            // two particles per thread and step (twice the loads and atomics
+            // in flight)
             const int lane = threadIdx.x & 31;
-            for (int pb = p0; pb < p1; pb += blockDim.x) {
-                const int p = pb + threadIdx.x;
-                float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-                float hh = 0.f;
-                if (p < p1) src.load(p, r, hh);
-                const int j = p < p1 ? sub_cell_id(r, w, g, c.b) : -1 - lane;
-                const unsigned same = __match_any_sync(~0u, j);
-                const int lead = __ffs(same) - 1;
-                int at = 0;
-                if (j >= 0 && lane == lead) at = atomicAdd(&cursor[c.hist_base + j], __popc(same));
-                at = __shfl_sync(~0u, at, lead);
-                if (j >= 0)
-                    scatter_one(T, c, j, at + __popc(same & ((1u << lane) - 1u)), r, hh, dst_pos, dst_h);
+            const unsigned lt = (1u << lane) - 1u;
+            for (int pb = p0; pb < p1; pb += 2 * blockDim.x) {
+                const int pa = pb + threadIdx.x, pc = pa + blockDim.x;
+                float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rc = ra;
+                float ha = 0.f, hc2 = 0.f;
+                if (pa < p1) src.load(pa, ra, ha);
+                if (pc < p1) src.load(pc, rc, hc2);
+                const int ja = pa < p1 ? sub_cell_id(ra, w, g, c.b) : -1 - lane;
+                const int jc = pc < p1 ? sub_cell_id(rc, w, g, c.b) : -1 - lane;
+                const unsigned sa = __match_any_sync(~0u, ja);
+                const unsigned sc = __match_any_sync(~0u, jc);
+                const int la = __ffs(sa) - 1, lc = __ffs(sc) - 1;
+                int ata = 0, atc = 0;
+                if (ja >= 0 && lane == la) ata = atomicAdd(&cursor[c.hist_base + ja], __popc(sa));
+                if (jc >= 0 && lane == lc) atc = atomicAdd(&cursor[c.hist_base + jc], __popc(sc));
+                ata = __shfl_sync(~0u, ata, la);
+                atc = __shfl_sync(~0u, atc, lc);
+                if (ja >= 0) scatter_one(T, c, ja, ata + __popc(sa & lt), ra, ha, dst_pos, dst_h);
+                if (jc >= 0) scatter_one(T, c, jc, atc + __popc(sc & lt), rc, hc2, dst_pos, dst_h);
             }
             continue;
         }
