@@ -72,7 +72,6 @@ struct FindSmem {
     // in p's ascending neighbour list is k mod 32, so the summation order
     // depends on the list alone (not on windows or work-unit composition)
     float qacc[kGroupMax][32];
-    unsigned short hits[C::WARPS][kHitBatch];
     int2 jobs[C::JOB_MAX];       // (first tree position, length <= 32)
     float4 q[kGroupMax];      // x, y, z, R_lo
     float qrhi[kGroupMax];
@@ -81,10 +80,18 @@ struct FindSmem {
     int qself[kGroupMax];     // sorted position of the query itself, or -1
     int qlow[kGroupMax];      // half rows: candidates below this sorted position are dropped
     int qcnt[kGroupMax];
-    int front[2][kFrontMax];  // walk frontiers
-    int fr_rx0[kFrontMax], fr_rx1[kFrontMax], fr_ry0[kFrontMax], fr_ny[kFrontMax];
-    int fr_rz0[kFrontMax], fr_row0[kFrontMax], fr_b[kFrontMax], fr_off[kFrontMax + 1];
-    int hist[256];
+    // Three arrays of three phases of a work unit share their storage: the
+    // walk's frontiers (once per unit, first), the histogram of the window
+    // planning (gather), and the hit positions of stage B (last, per window).
+    union {
+        struct {
+            int front[2][kFrontMax];  // walk frontiers
+            int fr_rx0[kFrontMax], fr_rx1[kFrontMax], fr_ry0[kFrontMax], fr_ny[kFrontMax];
+            int fr_rz0[kFrontMax], fr_row0[kFrontMax], fr_b[kFrontMax], fr_off[kFrontMax + 1];
+        };
+        int hist[256];
+        unsigned short hits[C::WARPS][kHitBatch];
+    };
     float box[13];            // PL[3] PH[3] QL[3] QH[3] T
     int njobs, nfront, nnext, ncand, kmin, kmax, range_ovf, ovf_lo, ovf_hi;
     int jfail, cover, gstart, gcount, whi, ctot;
@@ -746,7 +753,7 @@ __device__ __noinline__ bool split_unit(const TreeDev &T, int first, int gc, int
 }
 
 template <class C, bool DENS>
-__global__ void __launch_bounds__(C::NT, 1024 / C::NT) k_find(FindArgs A)
+__global__ void __launch_bounds__(C::NT, C::NT == 128 ? 9 : 1024 / C::NT) k_find(FindArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FindSmem<C> &S = *reinterpret_cast<FindSmem<C> *>(smem_raw);
