@@ -88,6 +88,38 @@ def _clustered(n, seed):
     return wl._pack(p[0], p[1], p[2], h, name="clustered")
 
 
+def test_near_pairs_grow_the_tree_buffers(bt, gpu, oracle):
+    """Pairs of nearly coincident particles at s = 1: each pair is a chain of
+    two-particle cells down to the level where its particles part (about 15
+    levels below the root, Algorithm 1 with b = 2), so the tree holds far
+    more internal nodes and sub-cells than the build's first estimate of its
+    buffers (3n/(s+1) nodes, 16n/s sub-cells).  The build grows them, builds
+    again, and gives the oracle's tree and the brute-force lists."""
+    rng = np.random.default_rng(61)
+    npair = 1500
+    a = (rng.random((3, npair)) * 0.9 + 0.05).astype(np.float32)
+    d = ((rng.random((3, npair)) - 0.5) * 2e-6).astype(np.float32)
+    p = np.concatenate([a, a + d], axis=1)
+    h = np.full(2 * npair, 0.02, np.float32)
+    s = wl._pack(p[0], p[1], p[2], h, name="near_pairs")
+    n = s.n
+    r = gpu.run_gpu(s, bucket_size=1, ngmax=64)
+    info = bt.btree_get_info(r["tree"])
+    assert info["num_nodes"] > 3 * n // 2 + 1024 + 1, "the first node estimate sufficed: no growth exercised"
+    assert info["num_slots"] > 16 * n + 4096
+    ot = oracle.OracleTree(s.x, s.y, s.z, bucket_size=1)
+    gpu.compare_trees(bt.btree_export(r["tree"]), ot.export(), n)
+    assert info["max_depth"] == ot.max_depth
+    ref_nb, ref_cnt = _brute(oracle, s, 64)
+    _assert_lists(r, ref_nb, ref_cnt)
+    # a rebuild in place (same sets, new positions: the asynchronous form)
+    # keeps the grown buffers and gives the same result for the same input
+    r2 = gpu.run_gpu(s, bucket_size=1, ngmax=64, tree=r["tree"])
+    _assert_lists(r2, ref_nb, ref_cnt)
+    assert bt.btree_get_info(r2["tree"])["num_nodes"] == info["num_nodes"]
+    r["tree"].free()
+
+
 @pytest.mark.parametrize("case", ["evrard", "plummer", "slab", "clustered"])
 def test_lists_match_brute_force_varied(bt, gpu, oracle, case):
     makers = {
