@@ -499,6 +499,40 @@ def _timed(fn, stream, steps, warmup=3):
     return e0.elapsed_time(e1) / steps
 
 
+def _batched_by_kind(bt, sets, kinds, tuner, dev, stream, ngmax, K):
+    """The tuned batched build + search of each kind of set alone (this
+    rank's sets), with the build and the search timed apart."""
+    import torch
+    from paper_1910_02639_gb300.batch import DeviceSets
+    out = {}
+    for kind in sorted(set(kinds)):
+        sub = [s for s, k in zip(sets, kinds) if k == kind]
+        ds = DeviceSets(sub, dev, ngmax)
+        p = tuner.params_for(sub)
+        ms = _timed(lambda: ds.run_batched(p, stream), stream, K)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        bms = fms = 0.0
+        for _ in range(K):
+            ev[0].record(stream)
+            ds._tree = bt.btree_build_batched(ds.x, ds.y, ds.z, ds.h, ds.offsets, ds.params_list(p),
+                                              stream=stream, tree=ds._tree)
+            ev[1].record(stream)
+            bt.btree_find_neighbors_density(ds._tree, ds.m, ds.ngmax, ds.nb, ds.cnt, ds.rho, stream=stream)
+            ev[2].record(stream)
+            ev[2].synchronize()
+            bms += ev[0].elapsed_time(ev[1]) / K
+            fms += ev[1].elapsed_time(ev[2]) / K
+        pairs = int(ds.cnt.to(torch.int64).sum().item())
+        out[kind] = {"sets": len(sub), "particles": int(sum(s.n for s in sub)), "pairs": pairs,
+                     "ms_per_step": ms, "pairs_per_s": pairs / (ms * 1e-3),
+                     "build_ms": bms, "find_ms": fms,
+                     "max_count": int(ds.cnt.max().item()) if sub else 0}
+        ds.free()
+        del ds
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_batched_section(args, bt, dev, stream, dist, rank, ws):
     """256 independent sets, sizes log-uniform in [1e3, 1e6] (uniform cube,
     1/r sphere, Plummer; 50-150 target neighbours), ngmax 256.  Each rank
@@ -547,6 +581,8 @@ def run_batched_section(args, bt, dev, stream, dist, rank, ws):
     plain_ms, batched_ms, tuned_ms, graph_ms = (reduce_max(dist, v, dev)
                                                 for v in (plain_ms, batched_ms, tuned_ms, graph_ms))
     ds.free()
+    del ds
+    by_kind = _batched_by_kind(bt, sets, [specs[i][0] for i in mine], tuner, dev, stream, ngmax, K)
     rate = lambda ms: all_pairs / (ms * 1e-3)
     table = {"%d,%d" % k: {kk: v.get(kk) for kk in ("bucket_size", "beta", "group_size", "find_compact",
                                                     "pack_leaves")}
@@ -568,6 +604,7 @@ def run_batched_section(args, bt, dev, stream, dist, rank, ws):
                       "form": "btree_build_find_batched with the tuned parameters: one CUDA graph "
                               "launch per step, level and ratio loops as device-side while-nodes",
                       "identical_to_plain": bool(same_g)},
+            "by_kind": by_kind,
             "speedup_batched_vs_plain": plain_ms / batched_ms,
             "speedup_graph_vs_plain": plain_ms / graph_ms,
             "speedup_tuned_vs_plain": plain_ms / tuned_ms,
